@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark: time-to-solution of the Stokes solve phase on GB300.
+
+Default workload (one "step" = one full solve to relative residual 1e-8):
+3D finite-difference Stokes, N=64 (262,144 nodes, 1,048,576 unknowns),
+lognormal viscosity sigma=0.5, K stored as 4x4 BSR FP64, monolithic
+block smoothed-aggregation AMG (damped Jacobi 1+1) + BiCGStab, FP64.
+Inputs are resident in HBM when the timed region starts; the matrix
+(257 MB) is larger than L2 (129 MB), so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c1|c3-fp64|c3-fp32|c3-bf16]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the same workload
+
+Multi-GPU: the solve does not shard in this build (replicas only): under
+torchrun every rank solves its own copy; value = max-over-ranks time per
+step divided by the number of ranks (aggregate time per solve).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "time-to-solution at rel. residual 1e-8 (solve phase)"
+UNIT = "ms"
+
+WORKLOADS = {
+    "c2": dict(system="c2", precision=0, desc=(
+        "3D FD Stokes N=64 (1,048,576 unknowns), lognormal mu sigma=0.5, 4x4 BSR FP64, "
+        "monolithic block SA-AMG (damped Jacobi 1+1) + BiCGStab, tol 1e-8")),
+    "c1": dict(system="c1", precision=0, desc=(
+        "3D FD Stokes N=16 (16,384 unknowns), mu=1, scalar CSR FP64, SA-AMG (SPAI0 1+1) + "
+        "BiCGStab, tol 1e-8")),
+    "c3-fp64": dict(system="c3", precision=0, desc=(
+        "3D FD Stokes N=128 (8,388,608 unknowns), lognormal mu sigma=1, Schur pressure "
+        "correction (3x3 velocity SA-AMG + scalar SA-AMG on S_hat, SPAI0) + GMRES(30) FP64, "
+        "hierarchy FP64")),
+    "c3-fp32": dict(system="c3", precision=1, desc="same as c3-fp64 with an FP32 hierarchy"),
+    "c3-bf16": dict(system="c3", precision=2, desc=(
+        "same as c3-fp64 with a BF16 hierarchy (FP32 accumulation)")),
+}
+
+
+def solver_params(gb, wl, **kw):
+    name = WORKLOADS[wl]["system"]
+    prec = WORKLOADS[wl]["precision"]
+    if name == "c3":
+        return gb.params_default(precond=gb.GBS_PC_SCHUR, krylov=gb.GBS_GMRES, precision=prec,
+                                 enable_adjoint=0, **kw)
+    relax = gb.GBS_SPAI0 if name == "c1" else gb.GBS_JACOBI
+    return gb.params_default(relax=relax, precision=prec, enable_adjoint=0, **kw)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_spmv_bytes(nbr, nnzb, B, sv=8, sx=8):
+    """x read once, y written once, int32 indices, values of every stored block."""
+    return nnzb * (B * B * sv + 4) + 4 * (nbr + 1) + nbr * B * (sx + sx)
+
+
+def vcycle_bytes(gb, H, B, precision):
+    """Algorithmic bytes of one V-cycle from the built hierarchy's sizes."""
+    sv = {0: 8, 1: 4, 2: 2}[precision]
+    sx = 8 if precision == 0 else 4
+    info = gb.hierarchy_info(H, 0)
+    total = 0.0
+    for l in range(info["nlevels"] - 1):
+        nb, nnz = info["n_brows"][l], info["nnzb"][l]
+        n = nb * B
+        nc = info["n_brows"][l + 1] * B
+        pP = gb.export_level_sizes(H, 0, l, 1)
+        pR = gb.export_level_sizes(H, 0, l, 2)
+        A = nnz * (B * B * sv + 4) + 4 * (nb + 1)
+        Pb = pP[2] * (B * B * sv + 4) + 4 * (pP[0] + 1)
+        Rb = pR[2] * (B * B * sv + 4) + 4 * (pR[0] + 1)
+        Mb = nb * B * B * sv
+        total += Mb + 2 * n * sx                      # x = M f
+        total += A + 3 * n * sx                       # r = f - A x
+        total += Rb + n * sx + nc * sx                # f_c = R r
+        total += Pb + nc * sx + 2 * n * sx            # x += P e_c
+        total += A + Mb + 3 * n * sx                  # x += M (f - A x)
+    ncs = info["n_brows"][-1] * B
+    total += ncs * ncs * sx + 2 * ncs * sx
+    if precision != 0:
+        n0 = info["n_brows"][0] * B
+        total += n0 * 2 * (8 + sx)                    # FP64 <-> FP32 casts
+    return total
+
+
+def time_cpu_oracle(system, wl, iters_to_scale, sample_iters=3, calibrate=False):
+    """The FP64 oracle on the host: setup (untimed), `sample_iters` Krylov
+    iterations timed, scaled to a full solve by `iters_to_scale` (or by the
+    oracle's own iteration count when calibrate=True)."""
+    from oracle import amg, bsr, krylov, schur
+    s = system
+    K = bsr.from_arrays(s.indptr, s.indices, s.data, s.bdim)
+    Ks = K.scipy().tocsr()
+    if s.method == "amg_bicgstab":
+        relax = "spai0" if s.name == "c1" else "jacobi"
+        Ho = amg.build_hierarchy(K, amg.AmgParams(relax=relax))
+
+        def run(maxiter):
+            return krylov.bicgstab(lambda v: Ks @ v, lambda v: amg.vcycle(Ho, v), s.b, tol=1e-8,
+                                   maxiter=maxiter)
+    else:
+        pc = schur.build(K, 3)
+
+        def run(maxiter):
+            return krylov.gmres(lambda v: Ks @ v, pc.apply, s.b, m=30, tol=1e-8, maxiter=maxiter)
+    full_iters = None
+    if calibrate:
+        _, info = run(10000)
+        full_iters = info.iters
+        iters_to_scale = full_iters
+    return run, iters_to_scale, full_iters, sample_iters
+
+
+def cpu_oracle_sample(run, sample_iters):
+    t0 = time.perf_counter()
+    run(sample_iters)
+    return (time.perf_counter() - t0) / sample_iters
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the FP64 CPU oracle on the same workload."""
+    if rank != 0:
+        return 0
+    import stokes_inputs as si
+    wl = args.workload
+    s = si.make_system(WORKLOADS[wl]["system"])
+    run, iters, full_iters, k = time_cpu_oracle(s, wl, None, sample_iters=args.sample_iters,
+                                                calibrate=True)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(run, 1)
+    per = []
+    for _ in range(args.steps):
+        per.append(cpu_oracle_sample(run, k))
+    per_it = float(np.mean(per))
+    value = per_it * full_iters * 1e3
+    sample = ("oracle setup untimed; per step %d Krylov iterations of the full-size workload "
+              "timed, scaled by the oracle's own iteration count (%d) to one solve" % (k, full_iters))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": value,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOADS[wl]["desc"]},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "iterations": full_iters}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbstokes", choices=["gbstokes", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--sample-iters", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import paper_2006_06052_gb300 as gb
+    import stokes_inputs as si
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        gb.build()
+    barrier(world)
+    gb.load_library()
+    wl = args.workload
+    spec = WORKLOADS[wl]
+    s = si.make_system(spec["system"])
+    prm = solver_params(gb, wl, use_graph=0 if args.no_graph else 1)
+    t0 = time.perf_counter()
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, s.bdim, prm)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    b = torch.as_tensor(s.b, device="cuda")
+    x = torch.zeros_like(b)
+
+    for _ in range(args.warmup):
+        x.zero_()
+        _, info = gb.solve(H, b, x)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = gb.kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        x.zero_()
+        _, info = gb.solve(H, b, x)
+        iters.append(info.iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = gb.kernel_launches() - l0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ms, world)
+    rel_res = info.rel_res
+    converged = bool(info.converged)
+
+    # end-to-end: pinned host b -> device, solve, device x -> pinned host, every step
+    bh = torch.as_tensor(s.b).pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    for _ in range(2):
+        b.copy_(bh, non_blocking=True)
+        x.zero_()
+        gb.solve(H, b, x)
+        xh.copy_(x, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.copy_(bh, non_blocking=True)
+        x.zero_()
+        gb.solve(H, b, x)
+        xh.copy_(x, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+
+    # dominant-kernel roofline: the FP64 outer BSR SpMV of K, timed alone
+    peak, peak_kind = load_peaks()
+    B = s.bdim
+    nbr = len(s.indptr) - 1
+    nnzb = len(s.indices)
+    y = torch.empty_like(b)
+    reps = 50
+    for _ in range(5):
+        gb.spmv(H, x, y)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        gb.spmv(H, x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    spmv_ms = e0.elapsed_time(e1) / reps
+    spmv_bytes = algorithmic_spmv_bytes(nbr, nnzb, B)
+    achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    traffic = None
+    tr_env = os.environ.get("GBS_SPMV_DRAM_BYTES")
+    if tr_env:
+        traffic = float(tr_env)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_outer (BSR %dx%d FP64 SpMV of K)" % (B, B),
+                "algorithmic_bytes": spmv_bytes, "ms": spmv_ms, "peak_kind": peak_kind}
+    # the V-cycle as a whole (monolithic AMG only)
+    vcycle = None
+    if spec["system"] != "c3":
+        for _ in range(3):
+            gb.apply_precond(H, b, y)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(20):
+            gb.apply_precond(H, b, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        vms = e0.elapsed_time(e1) / 20
+        vb = vcycle_bytes(gb, H, B, spec["precision"])
+        vcycle = {"ms": vms, "algorithmic_bytes": vb, "achieved_gbs": vb / (vms * 1e-3) / 1e9,
+                  "frac": vb / (vms * 1e-3) / 1e9 / peak}
+
+    out = {
+        "metric": METRIC, "value": ms_max / world, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if spec["precision"] == 0 else ("f64+f32" if spec["precision"] == 1
+                                                        else "f64+bf16"),
+        "data": "synthetic",
+        "config": {"workload": spec["desc"], "l2": "inputs larger than L2 (K = %.0f MB)"
+                   % (nnzb * (B * B * 8 + 4) / 1e6), "parallelism": "replicas" if world > 1 else "1gpu",
+                   "iterations": iters[-1], "rel_res": rel_res, "converged": converged,
+                   "setup_s": setup_s, "graph": not args.no_graph},
+        "e2e": {"value": e2e_ms / world, "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 8),
+                "d2h_bytes_per_step": int(x.numel() * 8)},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "vcycle": vcycle,
+        "clocks": clocks,
+        "hierarchy_bytes": gb.hierarchy_info(H)["bytes"],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        run, it_scale, _, k = time_cpu_oracle(s, wl, iters[-1], sample_iters=args.sample_iters)
+        per_it = cpu_oracle_sample(run, k)
+        out["cpu_baseline"] = {
+            "value": per_it * it_scale * 1e3, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": ("FP64 NumPy/SciPy oracle, 1 thread; setup untimed; %d Krylov iterations "
+                       "of the full-size workload timed and scaled to the GPU solve's %d "
+                       "iterations" % (k, it_scale))}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * gbstokes.h -- C ABI of the GB300 solve-phase library for Stokes
+ * saddle-point systems (Demidov, Mu, Wang, "Accelerating linear solvers
+ * for Stokes problems with C++ metaprogramming").
+ *
+ * The library solves K x = b, K a square matrix stored as CSR or block
+ * CSR (BSR) with bdim x bdim blocks, with a right-preconditioned Krylov
+ * method (BiCGStab or restarted GMRES) and one of two preconditioners:
+ *   - a monolithic smoothed-aggregation AMG V-cycle with SPAI0 or damped
+ *     Jacobi relaxation (Section 2.1, Listing "composition");
+ *   - the Schur pressure-correction preconditioner of Section 4,
+ *     Eq. SchurPC, with the pressure operator of Eq. SchurApprox; both
+ *     inner solves are one AMG V-cycle (velocity: bdim-1 = nvel blocks;
+ *     pressure: scalar).
+ * The AMG hierarchy may be stored in FP64, FP32 or BF16 (the last two
+ * accumulate in FP32); the outer Krylov vectors, dot products, norms and
+ * true-residual replacement are always FP64 (Section 4, mixed precision,
+ * Listing V4).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: gbs_status.  On failure gbs_last_error() returns a
+ *     thread-local message.  Invalid input is rejected before any device
+ *     work is queued.
+ *   - "host" pointers are read during the call only; the library copies
+ *     what it keeps.  "device" pointers are caller-owned CUDA global
+ *     memory on the current device, FP64, length n = n_brows * bdim,
+ *     16-byte aligned (GBS_ERR_INVALID otherwise).
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work of a call is ordered on it; a call blocks
+ *     only where it states so.
+ *   - Vectors are interleaved per block row (for the Stokes systems:
+ *     [u v w p] per node).
+ */
+#ifndef GBSTOKES_H
+#define GBSTOKES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbs_hierarchy gbs_hierarchy;   /* opaque, library-owned */
+
+typedef enum {
+  GBS_OK = 0,
+  GBS_NOT_CONVERGED = 1,    /* x and info are still written */
+  GBS_ERR_INVALID = -1,     /* bad argument or matrix (nothing queued) */
+  GBS_ERR_CUDA = -2,        /* a CUDA call failed */
+  GBS_ERR_OOM = -3,         /* device allocation failed */
+  GBS_ERR_BREAKDOWN = -4,   /* Krylov breakdown (rho or (rhat,v) = 0) */
+  GBS_ERR_NAN = -5          /* NaN/Inf in a norm */
+} gbs_status;
+
+enum { GBS_PC_AMG = 0, GBS_PC_SCHUR = 1 };
+enum { GBS_BICGSTAB = 0, GBS_GMRES = 1 };
+enum { GBS_FP64 = 0, GBS_FP32 = 1, GBS_BF16 = 2 };
+enum { GBS_SPAI0 = 0, GBS_JACOBI = 1 };
+
+/* A square or rectangular block-CSR matrix in HOST memory.
+ * row_ptr: int32[n_brows + 1], monotone, row_ptr[0] = 0.
+ * col_idx: int32[nnzb], strictly increasing within each block row,
+ *          each < n_bcols.
+ * vals:    double[nnzb * bdim * bdim], row-major blocks.
+ * bdim = 1 is plain CSR.  bdim in {1, 2, 3, 4}. */
+typedef struct {
+  int32_t n_brows;
+  int32_t n_bcols;
+  int32_t bdim;
+  int64_t nnzb;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const double* vals;
+} gbs_bsr;
+
+/* Runtime parameters; mirrors the nested params of Listing "params"
+ * (restart length, tolerance, strong-coupling threshold) as plain
+ * fields.  Obtain defaults with gbs_params_default(). */
+typedef struct {
+  int32_t precond;        /* GBS_PC_AMG | GBS_PC_SCHUR */
+  int32_t krylov;         /* GBS_BICGSTAB | GBS_GMRES */
+  int32_t restart;        /* GMRES restart length m (default 30, max 64) */
+  double tol;             /* relative true residual ||b-Kx||/||b|| (1e-8) */
+  int32_t maxiter;        /* default 1000 */
+  int32_t replace_every;  /* BiCGStab true-residual replacement period (50) */
+  int32_t precision;      /* hierarchy storage: GBS_FP64 | GBS_FP32 | GBS_BF16 */
+  double eps_strong;      /* strength threshold at level 0 (0.08), halved per level */
+  int32_t coarse_enough;  /* max scalar unknowns of the coarsest level (1000) */
+  int32_t max_levels;     /* default 10 */
+  int32_t npre, npost;    /* relaxation sweeps (1, 1); npost >= 1 */
+  int32_t relax;          /* smoother of the monolithic / velocity AMG */
+  int32_t relax_p;        /* smoother of the pressure AMG (Schur) */
+  double jacobi_omega;    /* damped Jacobi weight (0.72) */
+  int32_t smooth_P;       /* 1 smoothed aggregation, 0 plain aggregation */
+  int32_t power_iters;    /* power iterations for rho(D^-1 A) (20) */
+  int32_t nvel;           /* velocity unknowns per node for Schur (3) */
+  int32_t use_graph;      /* 1: replay each Krylov iteration as a CUDA graph */
+  int32_t enable_adjoint; /* 1: build transpose maps for solve_adjoint */
+  int32_t setup_only;     /* 1: build the host hierarchy only (no device work,
+                             no GPU needed); export/info work, solves do not */
+} gbs_params;
+
+typedef struct {
+  int32_t iters;          /* Krylov iterations (GMRES: Arnoldi steps) */
+  int32_t replacements;   /* true-residual replacements */
+  int32_t converged;
+  double rel_res;         /* final true ||b - K x|| / ||b|| in FP64 */
+  float ms;               /* device time of the solve (CUDA events) */
+  double* history;        /* optional caller host buffer of recurrence residuals */
+  int32_t history_cap;
+  int32_t history_len;
+} gbs_info;
+
+/* Fill *p with the defaults listed above. */
+gbs_status gbs_params_default(gbs_params* p);
+
+/* Build the preconditioner hierarchy on the host (smoothed aggregation,
+ * Galerkin coarse operators, SPAI0/Jacobi blocks, dense coarse inverse;
+ * Section 2: setup on builtin structures, then moved to the backend),
+ * cast it to params->precision and upload it, together with K in FP64
+ * and every work vector, to the current device.  After this call
+ * gbs_solve allocates no device memory.
+ * A: host BSR of K.  For GBS_PC_SCHUR, A->bdim must be nvel + 1 and
+ * each block row is one node with the pressure unknown last.
+ * stream: used for the uploads; the call synchronises it before return.
+ * out: receives the handle; free with gbs_destroy. */
+gbs_status gbs_build_hierarchy(const gbs_bsr* A, const gbs_params* params,
+                               void* stream, gbs_hierarchy** out);
+
+/* Solve K x = b.  b_dev: device FP64[n] (read only).  x_dev: device
+ * FP64[n], initial guess on entry, solution on return.  Blocks until the
+ * solve ends (one small device->host read per iteration decides
+ * convergence).  info may be NULL.  Returns GBS_NOT_CONVERGED when
+ * maxiter is reached (x still holds the last iterate). */
+gbs_status gbs_solve(gbs_hierarchy* h, const double* b_dev, double* x_dev,
+                     void* stream, gbs_info* info);
+
+/* Adjoint solve K^T lam = g with the same Krylov method and the
+ * transposed preconditioner (A_l^T through transpose maps, M_l^T, the
+ * same P and R since R = P^T, transposed coarse inverse; for Schur the
+ * same steps on K^T).  g_dev, lam_dev: device FP64[n]; lam is also the
+ * initial guess.  Requires enable_adjoint and a structurally symmetric
+ * block pattern at every level. */
+gbs_status gbs_solve_adjoint(gbs_hierarchy* h, const double* g_dev, double* lam_dev,
+                             void* stream, gbs_info* info);
+
+/* Sampled outer product on the stored pattern of K:
+ * grad[k*bdim*bdim + a*bdim + c] = alpha * lam[bdim*i + a] * x[bdim*j + c]
+ * for stored block k = (i, j).  With alpha = -1 this is dL/dK for
+ * x = K^-1 b and lam = K^-T dL/dx.  All pointers device FP64;
+ * grad has nnzb * bdim^2 entries.  Asynchronous on stream. */
+gbs_status gbs_sampled_outer(const gbs_hierarchy* h, const double* lam_dev,
+                             const double* x_dev, double alpha, double* grad_dev,
+                             void* stream);
+
+/* Replace the values of K (same pattern, device FP64[nnzb*bdim^2]); the
+ * preconditioner is kept as built.  Asynchronous on stream. */
+gbs_status gbs_update_values(gbs_hierarchy* h, const double* vals_dev, void* stream);
+
+/* y = K x (transpose != 0: y = K^T x) with the library's FP64 outer SpMV.
+ * x_dev, y_dev: device FP64[n].  Asynchronous on stream. */
+gbs_status gbs_spmv(const gbs_hierarchy* h, const double* x_dev, double* y_dev,
+                    int32_t transpose, void* stream);
+
+/* One application of the preconditioner: z = M^-1 r (transpose != 0:
+ * the transposed preconditioner).  r_dev, z_dev: device FP64[n].
+ * Asynchronous on stream. */
+gbs_status gbs_apply_precond(gbs_hierarchy* h, const double* r_dev, double* z_dev,
+                             int32_t transpose, void* stream);
+
+/* Hierarchy shape.  which: 0 monolithic / velocity AMG, 1 pressure AMG.
+ * Writes the number of levels (coarsest included) to *nlevels and, if
+ * the arrays are non-NULL, per level n_brows and nnzb of A_l (up to cap
+ * entries).  bytes: device bytes held by the hierarchy (may be NULL). */
+gbs_status gbs_hierarchy_info(const gbs_hierarchy* h, int32_t which, int32_t* nlevels,
+                              int32_t* n_brows, int64_t* nnzb, int32_t cap,
+                              int64_t* bytes);
+
+/* Copy level l (0 = finest) of AMG `which` to host arrays.  part: 0 = A,
+ * 1 = P, 2 = R, 3 = smoother blocks M (row_ptr/col_idx untouched),
+ * 4 = aggregate ids (written to col_idx, n_brows entries), 5 = dense
+ * coarse inverse (vals, n*n, row-major; level must be the coarsest).
+ * Pass NULL arrays to query sizes: *n_brows, *n_bcols, *nnzb are always
+ * written.  Values are the FP64 setup values (before any cast). */
+gbs_status gbs_export_level(const gbs_hierarchy* h, int32_t which, int32_t level,
+                            int32_t part, int32_t* n_brows, int32_t* n_bcols,
+                            int64_t* nnzb, int32_t* row_ptr, int32_t* col_idx,
+                            double* vals);
+
+/* Build a monolithic-AMG hierarchy from caller-supplied levels instead of
+ * running the setup: A[0..nlev-1] (A[0] = K), P[0..nlev-2], R[0..nlev-2],
+ * M[0..nlev-2] smoother blocks (double[n_brows_l * bdim^2] each), and
+ * the dense coarse inverse Ainv (double[n_L^2], row-major, n_L the
+ * scalar size of A[nlev-1]).  Other arguments as gbs_build_hierarchy
+ * (params->precond must be GBS_PC_AMG). */
+gbs_status gbs_import_hierarchy(const gbs_bsr* A, const gbs_bsr* P, const gbs_bsr* R,
+                                const double* const* M, const double* Ainv, int32_t nlev,
+                                const gbs_params* params, void* stream,
+                                gbs_hierarchy** out);
+
+/* Number of CUDA kernels this library has launched in this process (a
+ * replayed CUDA graph counts each of its kernel nodes).  Telemetry only. */
+int64_t gbs_kernel_launches(void);
+
+/* Free everything the handle owns.  Synchronises the device. */
+gbs_status gbs_destroy(gbs_hierarchy* h);
+
+/* Thread-local message of the last failure ("" if none). */
+const char* gbs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBSTOKES_H */

@@ -1,0 +1,441 @@
+// Device AMG hierarchy, V-cycle and Schur pressure correction, templated
+// on the storage form (FP64 / FP32 / BF16 values).  Included once per
+// form by amg_fp64.cu, amg_fp32.cu, amg_bf16.cu.
+//
+// V-cycle (Section 2.1: AMG with SPAI0 relaxation on every level): one
+// zero-guess pre-sweep x = M f, residual r = f - A x, restriction
+// f_c = R r, recursive coarse correction, prolongation x += P e_c, one
+// post-sweep x += M (f - A x); dense inverse on the coarsest level.  The
+// transposed cycle uses A^T (transpose map), M^T, the same P and R
+// (R = P^T) and the transposed coarse inverse, with the sweep counts
+// swapped, which makes it the exact adjoint of the forward cycle.
+//
+// Schur pressure correction (Section 4, Eq. SchurPC, one V-cycle per
+// inner solve): u* = V_A(r_u); p = V_S(r_p - D u*); u = V_A(r_u - G p).
+// The transposed application runs the same steps on K^T = [A^T D^T; G^T
+// C^T] with transposed V-cycles.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "device.hpp"
+#include "kernels.cuh"
+
+namespace gbs {
+
+template <int P>
+struct FormT;
+template <>
+struct FormT<0> {
+  using VT = double;  // stored values
+  using ST = double;  // V-cycle vectors and accumulation
+};
+template <>
+struct FormT<1> {
+  using VT = float;
+  using ST = float;
+};
+template <>
+struct FormT<2> {
+  using VT = __nv_bfloat16;
+  using ST = float;
+};
+
+template <class VT>
+inline VT cast_host(double v);
+template <>
+inline double cast_host<double>(double v) { return v; }
+template <>
+inline float cast_host<float>(double v) { return (float)v; }
+template <>
+inline __nv_bfloat16 cast_host<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+
+template <class VT>
+std::vector<VT> cast_vec(const std::vector<double>& v) {
+  std::vector<VT> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = cast_host<VT>(v[i]);
+  return o;
+}
+
+template <class VT>
+DevBsr<VT> upload_bsr(Arena& ar, const HBsr& H, bool with_tmap, cudaStream_t s,
+                      std::vector<std::vector<VT>>& keep) {
+  DevBsr<VT> d;
+  d.nbr = H.nbr;
+  d.nbc = H.nbc;
+  d.rp = ar.upload(H.ptr.data(), H.ptr.size(), s);
+  d.col = ar.upload(H.col.data(), H.col.size(), s);
+  keep.push_back(cast_vec<VT>(H.val));
+  d.val = ar.upload(keep.back().data(), keep.back().size(), s);
+  if (with_tmap) {
+    std::vector<int32_t> tm;
+    if (!transpose_map(H, tm))
+      throw SetupError{"block pattern is not structurally symmetric (needed for the adjoint)"};
+    d.tmap = ar.upload(tm.data(), tm.size(), s);
+  }
+  return d;
+}
+
+// ------------------------------------------------------------ launch helpers
+template <int B, bool TR, int MODE, class VT, class XT, class YT, class AT>
+void spmv_B(const DevBsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
+  if (A.nbr == 0) return;
+  k_spmv<B, TR, MODE, VT, XT, YT, AT><<<grid_for(row_threads<B>(A.nbr)), 256, 0, s>>>(A, x, f, y);
+}
+template <bool TR, int MODE, class VT, class XT, class YT, class AT>
+void spmv(int B, const DevBsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
+  switch (B) {
+    case 1: spmv_B<1, TR, MODE, VT, XT, YT, AT>(A, x, f, y, s); break;
+    case 2: spmv_B<2, TR, MODE, VT, XT, YT, AT>(A, x, f, y, s); break;
+    case 3: spmv_B<3, TR, MODE, VT, XT, YT, AT>(A, x, f, y, s); break;
+    case 4: spmv_B<4, TR, MODE, VT, XT, YT, AT>(A, x, f, y, s); break;
+  }
+  GBS_LAUNCH_CHECK();
+}
+template <bool TR, class VT, class XT, class AT>
+void relax(int B, const DevBsr<VT>& A, const VT* M, const XT* f, const XT* x, XT* xo,
+           cudaStream_t s) {
+  if (A.nbr == 0) return;
+#define GBS_RELAX(BB) \
+  k_relax<BB, TR, VT, XT, AT><<<grid_for(row_threads<BB>(A.nbr)), 256, 0, s>>>(A, M, f, x, xo)
+  switch (B) {
+    case 1: GBS_RELAX(1); break;
+    case 2: GBS_RELAX(2); break;
+    case 3: GBS_RELAX(3); break;
+    case 4: GBS_RELAX(4); break;
+  }
+#undef GBS_RELAX
+  GBS_LAUNCH_CHECK();
+}
+template <bool TR, class VT, class XT, class AT>
+void mapply(int B, int nbr, const VT* M, const XT* f, XT* x, cudaStream_t s) {
+  if (nbr == 0) return;
+#define GBS_MAP(BB) \
+  k_mapply<BB, TR, VT, XT, AT><<<grid_for(row_threads<BB>(nbr)), 256, 0, s>>>(nbr, M, f, x)
+  switch (B) {
+    case 1: GBS_MAP(1); break;
+    case 2: GBS_MAP(2); break;
+    case 3: GBS_MAP(3); break;
+    case 4: GBS_MAP(4); break;
+  }
+#undef GBS_MAP
+  GBS_LAUNCH_CHECK();
+}
+
+template <class TI, class TO>
+void cast(int64_t n, const TI* in, TO* out, cudaStream_t s) {
+  if (n == 0) return;
+  unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_cast<TI, TO><<<g, 256, 0, s>>>(n, in, out);
+  GBS_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ AMG
+template <int P>
+struct DevAmg {
+  using VT = typename FormT<P>::VT;
+  using ST = typename FormT<P>::ST;
+  using AT = ST;
+
+  struct Lev {
+    DevBsr<VT> A, Pm, R;
+    const VT* M = nullptr;
+    ST *f = nullptr, *r = nullptr, *x = nullptr, *xt = nullptr, *e = nullptr;
+    int64_t n = 0;
+    int64_t nnzb_A = 0, nnzb_P = 0, nnzb_R = 0;
+  };
+  int B = 1;
+  int npre = 1, npost = 1;
+  std::vector<Lev> lev;        // lev.back() is the coarsest (no A/P/R/M used)
+  const ST* Ainv = nullptr;    // coarse inverse (ST precision)
+  const ST* AinvT = nullptr;
+  int nc = 0;                  // scalar size of the coarsest level
+  Arena ar;
+
+  void build(const HAmg& H, const PrecondOptions& o, cudaStream_t s) {
+    B = H.B;
+    npre = o.npre;
+    npost = o.npost;
+    std::vector<std::vector<VT>> keep;
+    for (size_t l = 0; l < H.levels.size(); ++l) {
+      const HLevel& h = H.levels[l];
+      Lev L;
+      L.n = (int64_t)h.A.nbr * B;
+      L.A = upload_bsr<VT>(ar, h.A, o.tmaps, s, keep);
+      L.Pm = upload_bsr<VT>(ar, h.P, false, s, keep);
+      L.R = upload_bsr<VT>(ar, h.R, false, s, keep);
+      keep.push_back(cast_vec<VT>(h.M));
+      L.M = ar.upload(keep.back().data(), keep.back().size(), s);
+      L.f = ar.alloc<ST>(L.n);
+      L.r = ar.alloc<ST>(L.n);
+      L.x = ar.alloc<ST>(L.n);
+      L.xt = ar.alloc<ST>(L.n);
+      L.e = ar.alloc<ST>(L.n);
+      L.nnzb_A = h.A.nnzb();
+      L.nnzb_P = h.P.nnzb();
+      L.nnzb_R = h.R.nnzb();
+      lev.push_back(L);
+    }
+    Lev C;
+    C.n = (int64_t)H.Ac.nbr * B;
+    C.nnzb_A = H.Ac.nnzb();
+    C.f = ar.alloc<ST>(C.n);
+    C.e = ar.alloc<ST>(C.n);
+    C.x = ar.alloc<ST>(C.n);
+    lev.push_back(C);
+    nc = (int)C.n;
+    std::vector<ST> inv(H.Ainv.size()), invT(H.Ainv.size());
+    for (int i = 0; i < nc; ++i)
+      for (int j = 0; j < nc; ++j) {
+        inv[(size_t)i * nc + j] = (ST)H.Ainv[(size_t)i * nc + j];
+        invT[(size_t)j * nc + i] = (ST)H.Ainv[(size_t)i * nc + j];
+      }
+    Ainv = ar.upload(inv.data(), inv.size(), s);
+    AinvT = ar.upload(invT.data(), invT.size(), s);
+    GBS_CUDA(cudaStreamSynchronize(s));  // host staging buffers die here
+  }
+
+  int64_t n0() const { return lev[0].n; }
+
+  // out = V(f) at level l; f and out are ST vectors of that level's size.
+  template <bool TR>
+  void cycle(size_t l, const ST* f, ST* out, cudaStream_t s) {
+    if (l + 1 == lev.size()) {
+      const ST* Ai = TR ? AinvT : Ainv;
+      k_gemv<ST, ST, AT><<<grid_for((int64_t)nc * 32), 256, 0, s>>>(nc, Ai, f, out);
+      GBS_LAUNCH_CHECK();
+      return;
+    }
+    Lev& L = lev[l];
+    const int nb = L.A.nbr;
+    const int pre = TR ? npost : npre;
+    const int post = TR ? npre : npost;
+    ST* x = L.x;
+    ST* xt = L.xt;
+    if (pre >= 1) {
+      mapply<TR, VT, ST, AT>(B, nb, L.M, f, x, s);
+      for (int it = 1; it < pre; ++it) {
+        relax<TR, VT, ST, AT>(B, L.A, L.M, f, x, xt, s);
+        std::swap(x, xt);
+      }
+    } else {
+      GBS_CUDA(cudaMemsetAsync(x, 0, sizeof(ST) * L.n, s));
+    }
+    spmv<TR, SPMV_RESID, VT, ST, ST, AT>(B, L.A, x, f, L.r, s);
+    Lev& Cn = lev[l + 1];
+    spmv<false, SPMV_SET, VT, ST, ST, AT>(B, L.R, L.r, (const ST*)nullptr, Cn.f, s);
+    cycle<TR>(l + 1, Cn.f, Cn.e, s);
+    spmv<false, SPMV_ADD, VT, ST, ST, AT>(B, L.Pm, Cn.e, (const ST*)nullptr, x, s);
+    for (int it = 0; it < post; ++it) {
+      ST* dst = (it + 1 == post) ? out : xt;
+      relax<TR, VT, ST, AT>(B, L.A, L.M, f, x, dst, s);
+      std::swap(x, xt);
+    }
+  }
+
+  void vcycle(const ST* f, ST* out, bool tr, cudaStream_t s) {
+    if (tr) cycle<true>(0, f, out, s);
+    else cycle<false>(0, f, out, s);
+  }
+
+  double bytes_per_cycle() const {
+    double b = 0;
+    const double sv = sizeof(VT), sx = sizeof(ST);
+    for (size_t l = 0; l + 1 < lev.size(); ++l) {
+      const Lev& L = lev[l];
+      const double nb = (double)L.A.nbr;
+      const double Abytes = L.nnzb_A * (B * B * sv + 4) + 4 * (nb + 1);
+      const double Pbytes = L.nnzb_P * (B * B * sv + 4) + 4 * (nb + 1);
+      const double Rbytes = L.nnzb_R * (B * B * sv + 4) + 4 * (L.R.nbr + 1);
+      const double Mbytes = nb * B * B * sv;
+      // mapply (M, f, x) + resid (A, x, f, r) + restrict (R, r, fc)
+      // + prolong (P, ec, x rw) + relax (A, M, f, x, out)
+      b += Mbytes + 2 * L.n * sx;
+      b += Abytes + 3 * L.n * sx;
+      b += Rbytes + L.n * sx + lev[l + 1].n * sx;
+      b += Pbytes + lev[l + 1].n * sx + 2 * L.n * sx;
+      b += Abytes + Mbytes + 3 * L.n * sx;
+    }
+    b += (double)nc * nc * sx + 2.0 * nc * sx;
+    return b;
+  }
+};
+
+template <int P>
+struct AmgPrecond final : DevPrecond {
+  using ST = typename FormT<P>::ST;
+  DevAmg<P> amg;
+  ST *fin = nullptr, *fout = nullptr;  // mixed forms: FP32 staging of r and z
+  Arena ar;
+  void init(const HAmg& H, const PrecondOptions& o, cudaStream_t s) {
+    amg.build(H, o, s);
+    if constexpr (!std::is_same<ST, double>::value) {
+      fin = ar.alloc<ST>(amg.n0());
+      fout = ar.alloc<ST>(amg.n0());
+    }
+  }
+  void apply(const double* r, double* z, bool tr, cudaStream_t s) override {
+    if constexpr (std::is_same<ST, double>::value) {
+      amg.vcycle(r, z, tr, s);
+    } else {
+      cast<double, ST>(amg.n0(), r, fin, s);
+      amg.vcycle(fin, fout, tr, s);
+      cast<ST, double>(amg.n0(), fout, z, s);
+    }
+  }
+  int64_t bytes() const override { return amg.ar.bytes + ar.bytes; }
+  int nlevels(int which) const override { return which == 0 ? (int)amg.lev.size() : 0; }
+  int64_t level_rows(int, int l) const override { return amg.lev[l].n / amg.B; }
+  int64_t level_nnzb(int, int l) const override { return amg.lev[l].nnzb_A; }
+  double bytes_per_apply() const override {
+    double b = amg.bytes_per_cycle();
+    if constexpr (!std::is_same<ST, double>::value) b += amg.n0() * 2.0 * (8 + sizeof(ST));
+    return b;
+  }
+};
+
+// ------------------------------------------------------------- Schur kernels
+// fu[i*NV + c] = r[i*(NV+1) + c]
+template <int NV, class ST>
+__global__ void k_gather_u(int nn, const double* __restrict__ r, ST* __restrict__ fu) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nn * NV;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = t / NV;
+    int c = (int)(t - i * NV);
+    fu[t] = (ST)r[i * (NV + 1) + c];
+  }
+}
+// q_i = r_p,i - sum_k Dblk(k) . u_{col k};  Dblk(k) = D[k] or (transposed) G[tmap k]
+template <int NV, class VT, class ST>
+__global__ void k_schur_q(DevBsr<VT> D, const VT* __restrict__ Dval, bool tr,
+                          const double* __restrict__ r, const ST* __restrict__ u,
+                          ST* __restrict__ q) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.nbr; i += gridDim.x * blockDim.x) {
+    ST acc = ST(0);
+    for (int k = D.rp[i]; k < D.rp[i + 1]; ++k) {
+      const int j = D.col[k];
+      const int kb = tr ? D.tmap[k] : k;
+#pragma unroll
+      for (int c = 0; c < NV; ++c) acc += cvt<ST>(Dval[(size_t)kb * NV + c]) * u[(size_t)j * NV + c];
+    }
+    q[i] = (ST)r[(size_t)i * (NV + 1) + NV] - acc;
+  }
+}
+// fu2[i*NV + c] = fu[i*NV + c] - sum_k Gblk(k)[c] p_{col k};  Gblk = G[k] or D[tmap k]
+template <int NV, class VT, class ST>
+__global__ void k_schur_u(DevBsr<VT> G, const VT* __restrict__ Gval, bool tr,
+                          const ST* __restrict__ fu, const ST* __restrict__ p,
+                          ST* __restrict__ fu2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.nbr; i += gridDim.x * blockDim.x) {
+    ST acc[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) acc[c] = fu[(size_t)i * NV + c];
+    for (int k = G.rp[i]; k < G.rp[i + 1]; ++k) {
+      const int j = G.col[k];
+      const int kb = tr ? G.tmap[k] : k;
+      const ST pj = p[j];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) acc[c] -= cvt<ST>(Gval[(size_t)kb * NV + c]) * pj;
+    }
+#pragma unroll
+    for (int c = 0; c < NV; ++c) fu2[(size_t)i * NV + c] = acc[c];
+  }
+}
+template <int NV, class ST>
+__global__ void k_scatter_z(int nn, const ST* __restrict__ u, const ST* __restrict__ p,
+                            double* __restrict__ z) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nn * (NV + 1);
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = t / (NV + 1);
+    int c = (int)(t - i * (NV + 1));
+    z[t] = c < NV ? (double)u[i * NV + c] : (double)p[i];
+  }
+}
+
+template <int P>
+struct SchurPrecond final : DevPrecond {
+  using VT = typename FormT<P>::VT;
+  using ST = typename FormT<P>::ST;
+  DevAmg<P> A, S;
+  DevBsr<VT> G, D;  // share K's pattern; val = coupling values
+  int nv = 3, nn = 0;
+  ST *fu = nullptr, *fu2 = nullptr, *u1 = nullptr, *u = nullptr, *q = nullptr, *p = nullptr;
+  Arena ar;
+  int64_t nnzb = 0;
+
+  void init(const HSchur& Hs, const HAmg& HA, const HAmg& HS, const PrecondOptions& o,
+            cudaStream_t s) {
+    nv = Hs.nvel;
+    nn = Hs.C.nbr;
+    nnzb = Hs.C.nnzb();
+    A.build(HA, o, s);
+    S.build(HS, o, s);
+    std::vector<std::vector<VT>> keep;
+    G = upload_bsr<VT>(ar, Hs.G, o.tmaps, s, keep);
+    D.nbr = Hs.D.nbr;
+    D.nbc = Hs.D.nbc;
+    D.rp = G.rp;
+    D.col = G.col;
+    D.tmap = G.tmap;
+    keep.push_back(cast_vec<VT>(Hs.D.val));
+    D.val = ar.upload(keep.back().data(), keep.back().size(), s);
+    fu = ar.alloc<ST>((size_t)nn * nv);
+    fu2 = ar.alloc<ST>((size_t)nn * nv);
+    u1 = ar.alloc<ST>((size_t)nn * nv);
+    u = ar.alloc<ST>((size_t)nn * nv);
+    q = ar.alloc<ST>(nn);
+    p = ar.alloc<ST>(nn);
+    GBS_CUDA(cudaStreamSynchronize(s));
+  }
+
+  template <int NV>
+  void run(const double* r, double* z, bool tr, cudaStream_t s) {
+    const unsigned g = grid_for((int64_t)nn * NV);
+    const unsigned gn = grid_for(nn);
+    k_gather_u<NV, ST><<<g, 256, 0, s>>>(nn, r, fu);
+    GBS_LAUNCH_CHECK();
+    A.vcycle(fu, u1, tr, s);
+    // forward: q = r_p - D u1; transposed: q = r_p - G^T u1
+    k_schur_q<NV, VT, ST><<<gn, 256, 0, s>>>(D, tr ? G.val : D.val, tr, r, u1, q);
+    GBS_LAUNCH_CHECK();
+    S.vcycle(q, p, tr, s);
+    // forward: fu2 = fu - G p; transposed: fu2 = fu - D^T p
+    k_schur_u<NV, VT, ST><<<gn, 256, 0, s>>>(G, tr ? D.val : G.val, tr, fu, p, fu2);
+    GBS_LAUNCH_CHECK();
+    A.vcycle(fu2, u, tr, s);
+    k_scatter_z<NV, ST><<<grid_for((int64_t)nn * (NV + 1)), 256, 0, s>>>(nn, u, p, z);
+    GBS_LAUNCH_CHECK();
+  }
+
+  void apply(const double* r, double* z, bool tr, cudaStream_t s) override {
+    switch (nv) {
+      case 1: run<1>(r, z, tr, s); break;
+      case 2: run<2>(r, z, tr, s); break;
+      case 3: run<3>(r, z, tr, s); break;
+    }
+  }
+  int64_t bytes() const override { return A.ar.bytes + S.ar.bytes + ar.bytes; }
+  int nlevels(int which) const override {
+    return which == 0 ? (int)A.lev.size() : (int)S.lev.size();
+  }
+  int64_t level_rows(int which, int l) const override {
+    return which == 0 ? A.lev[l].n / A.B : S.lev[l].n;
+  }
+  int64_t level_nnzb(int which, int l) const override {
+    return which == 0 ? A.lev[l].nnzb_A : S.lev[l].nnzb_A;
+  }
+  double bytes_per_apply() const override {
+    const double sv = sizeof(VT), sx = sizeof(ST);
+    double b = 2 * A.bytes_per_cycle() + S.bytes_per_cycle();
+    // gather, two couplings, scatter
+    b += nn * nv * (8 + sx);
+    b += nnzb * (nv * sv + 4) + nn * nv * sx + nn * (8 + sx);
+    b += nnzb * (nv * sv + 4) + nn * sx + 2.0 * nn * nv * sx;
+    b += nn * (nv + 1) * 8 + nn * (nv + 1) * sx;
+    return b;
+  }
+};
+
+}  // namespace gbs

@@ -1,0 +1,815 @@
+// C ABI (include/gbstokes.h): hierarchy build/import, BiCGStab and
+// GMRES drivers on the FP64 outer operator, adjoint solve, sampled outer
+// product.  The Krylov loops run on the host and launch device kernels;
+// iteration scalars stay on the device and one small device-to-host read
+// per iteration decides convergence.  Optionally each BiCGStab iteration
+// is replayed from a captured CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/gbstokes.h"
+#include "amg_dev.cuh"
+#include "device.hpp"
+#include "outer.cuh"
+#include "setup.hpp"
+
+namespace gbs {
+
+thread_local std::string g_err;
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+struct Handle {
+  gbs_params prm{};
+  int B = 1;
+  int64_t n = 0;
+  HBsr Kh;                       // host copy of K (pattern + FP64 values)
+  DevBsr<double> K;
+  double* Kval = nullptr;
+  std::unique_ptr<DevPrecond> pc;
+  bool schur = false;
+  HAmg H, HA, HS;                // host hierarchies (export)
+  HSchur Sh;
+  Arena ar;
+  // work vectors
+  double *r, *rhat, *p, *ph, *v, *s, *sh, *t, *xi, *bi;
+  double *V = nullptr, *hcol, *hcol2, *ydev, *z, *u;
+  int m = 30;
+  double* sc;
+  double* sc_host = nullptr;     // pinned
+  double* h_host = nullptr;      // pinned
+  Red red;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // BiCGStab iteration, fwd / adjoint
+  int64_t gnodes[2] = {0, 0};                     // kernels per graph replay
+  ~Handle() {
+    for (auto& g : gexec)
+      if (g) cudaGraphExecDestroy(g);
+    if (cap) cudaStreamDestroy(cap);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (sc_host) cudaFreeHost(sc_host);
+    if (h_host) cudaFreeHost(h_host);
+  }
+};
+
+namespace {
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+unsigned vgrid(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+}
+
+HBsr from_c(const gbs_bsr* A) {
+  if (!A) throw SetupError{"null matrix"};
+  if (A->n_brows < 0 || A->n_bcols < 0 || A->nnzb < 0 || A->bdim < 1 || A->bdim > 4)
+    throw SetupError{"bad matrix dimensions"};
+  if (!A->row_ptr || (A->nnzb > 0 && (!A->col_idx || !A->vals)))
+    throw SetupError{"null matrix array"};
+  if (A->nnzb > INT32_MAX) throw SetupError{"nnzb exceeds int32 range"};
+  HBsr H;
+  H.nbr = A->n_brows;
+  H.nbc = A->n_bcols;
+  H.br = H.bc = A->bdim;
+  H.ptr.assign(A->row_ptr, A->row_ptr + A->n_brows + 1);
+  if (H.ptr.back() != A->nnzb) throw SetupError{"row_ptr[n_brows] != nnzb"};
+  H.col.assign(A->col_idx, A->col_idx + A->nnzb);
+  H.val.assign(A->vals, A->vals + A->nnzb * A->bdim * A->bdim);
+  return H;
+}
+
+void check_params(const gbs_params* p) {
+  if (!p) throw SetupError{"null params"};
+  if (p->precond != GBS_PC_AMG && p->precond != GBS_PC_SCHUR) throw SetupError{"bad precond"};
+  if (p->krylov != GBS_BICGSTAB && p->krylov != GBS_GMRES) throw SetupError{"bad krylov"};
+  if (p->restart < 1 || p->restart > 64) throw SetupError{"restart must be in 1..64"};
+  if (!(p->tol > 0.0)) throw SetupError{"tol must be > 0"};
+  if (p->maxiter < 1) throw SetupError{"maxiter must be >= 1"};
+  if (p->replace_every < 1) throw SetupError{"replace_every must be >= 1"};
+  if (p->precision < GBS_FP64 || p->precision > GBS_BF16) throw SetupError{"bad precision"};
+  if (p->npre < 0 || p->npost < 1) throw SetupError{"need npre >= 0 and npost >= 1"};
+  if (p->relax != GBS_SPAI0 && p->relax != GBS_JACOBI) throw SetupError{"bad relax"};
+  if (p->relax_p != GBS_SPAI0 && p->relax_p != GBS_JACOBI) throw SetupError{"bad relax_p"};
+  if (p->max_levels < 1 || p->coarse_enough < 1) throw SetupError{"bad level limits"};
+  if (p->precond == GBS_PC_SCHUR && (p->nvel < 1 || p->nvel > 3))
+    throw SetupError{"nvel must be in 1..3"};
+}
+
+AmgSetupParams amg_prm(const gbs_params* p, int relax) {
+  AmgSetupParams a;
+  a.eps_strong = p->eps_strong;
+  a.coarse_enough = p->coarse_enough;
+  a.max_levels = p->max_levels;
+  a.relax = relax;
+  a.jacobi_omega = p->jacobi_omega;
+  a.smooth_P = p->smooth_P != 0;
+  a.power_iters = p->power_iters;
+  return a;
+}
+
+PrecondOptions pc_opts(const gbs_params* p) {
+  PrecondOptions o;
+  o.precision = p->precision;
+  o.npre = p->npre;
+  o.npost = p->npost;
+  o.tmaps = p->enable_adjoint != 0;
+  return o;
+}
+
+void alloc_work(Handle& h, cudaStream_t s) {
+  Arena& a = h.ar;
+  const int64_t n = h.n;
+  h.Kval = a.upload(h.Kh.val.data(), h.Kh.val.size(), s);
+  h.K.nbr = h.Kh.nbr;
+  h.K.nbc = h.Kh.nbc;
+  h.K.rp = a.upload(h.Kh.ptr.data(), h.Kh.ptr.size(), s);
+  h.K.col = a.upload(h.Kh.col.data(), h.Kh.col.size(), s);
+  h.K.val = h.Kval;
+  if (h.prm.enable_adjoint) {
+    std::vector<int32_t> tm;
+    if (!transpose_map(h.Kh, tm))
+      throw SetupError{"K's block pattern is not structurally symmetric (needed for the adjoint)"};
+    h.K.tmap = a.upload(tm.data(), tm.size(), s);
+  }
+  for (double** q : {&h.r, &h.rhat, &h.p, &h.ph, &h.v, &h.s, &h.sh, &h.t, &h.xi, &h.bi})
+    *q = a.alloc<double>(n);
+  h.m = h.prm.restart;
+  if (h.prm.krylov == GBS_GMRES) {
+    h.V = a.alloc<double>((size_t)(h.m + 1) * n);
+    h.z = a.alloc<double>(n);
+    h.u = a.alloc<double>(n);
+  }
+  h.hcol = a.alloc<double>(MAX_DOTS);
+  h.hcol2 = a.alloc<double>(MAX_DOTS);
+  h.ydev = a.alloc<double>(MAX_DOTS);
+  h.sc = a.alloc<double>(S_COUNT);
+  GBS_CUDA(cudaMemsetAsync(h.sc, 0, sizeof(double) * S_COUNT, s));
+  h.red.sc = h.sc;
+  h.red.partials = a.alloc<double>((size_t)RED_BLOCKS * MAX_DOTS);
+  h.red.counter = a.alloc<unsigned>(16);
+  GBS_CUDA(cudaMemsetAsync(h.red.counter, 0, sizeof(unsigned) * 16, s));
+  GBS_CUDA(cudaMallocHost(&h.sc_host, sizeof(double) * S_COUNT));
+  GBS_CUDA(cudaMallocHost(&h.h_host, sizeof(double) * MAX_DOTS));
+  GBS_CUDA(cudaEventCreate(&h.ev0));
+  GBS_CUDA(cudaEventCreate(&h.ev1));
+  GBS_CUDA(cudaStreamCreateWithFlags(&h.cap, cudaStreamNonBlocking));
+  GBS_CUDA(cudaStreamSynchronize(s));
+}
+
+// ----------------------------------------------------------- outer kernels
+template <bool TR, int MODE>
+void outer_B(const Handle& h, const double* x, const double* f, double* y, const double* w0,
+             const double* w1, int slot, int op, bool reduce, cudaStream_t s) {
+  const Red& R = h.red;
+#define GBS_OUT(BB) \
+  k_outer<BB, TR, MODE><<<RED_BLOCKS, RED_THREADS, 0, s>>>(h.K, x, f, y, w0, w1, R, slot, op, reduce)
+  switch (h.B) {
+    case 1: GBS_OUT(1); break;
+    case 2: GBS_OUT(2); break;
+    case 3: GBS_OUT(3); break;
+    case 4: GBS_OUT(4); break;
+  }
+#undef GBS_OUT
+  GBS_LAUNCH_CHECK();
+}
+void outer(const Handle& h, bool tr, int mode, const double* x, const double* f, double* y,
+           const double* w0, const double* w1, int slot, int op, bool reduce, cudaStream_t s) {
+  if (tr) {
+    if (mode == SPMV_RESID) outer_B<true, SPMV_RESID>(h, x, f, y, w0, w1, slot, op, reduce, s);
+    else outer_B<true, SPMV_SET>(h, x, f, y, w0, w1, slot, op, reduce, s);
+  } else {
+    if (mode == SPMV_RESID) outer_B<false, SPMV_RESID>(h, x, f, y, w0, w1, slot, op, reduce, s);
+    else outer_B<false, SPMV_SET>(h, x, f, y, w0, w1, slot, op, reduce, s);
+  }
+}
+
+void read_scalars(Handle& h, cudaStream_t s) {
+  GBS_CUDA(cudaMemcpyAsync(h.sc_host, h.sc, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+  GBS_CUDA(cudaStreamSynchronize(s));
+}
+
+// One BiCGStab iteration (all device work, no host reads).
+void bicg_iteration(Handle& h, bool tr, cudaStream_t s) {
+  const int64_t n = h.n;
+  const unsigned g = vgrid(n);
+  k_bicg_p<<<g, 256, 0, s>>>(n, h.r, h.v, h.p, h.sc);
+  GBS_LAUNCH_CHECK();
+  h.pc->apply(h.p, h.ph, tr, s);
+  outer(h, tr, SPMV_SET, h.ph, nullptr, h.v, h.rhat, nullptr, 0, FIN_ALPHA, true, s);
+  k_bicg_s<<<g, 256, 0, s>>>(n, h.r, h.v, h.s, h.sc);
+  GBS_LAUNCH_CHECK();
+  h.pc->apply(h.s, h.sh, tr, s);
+  outer(h, tr, SPMV_SET, h.sh, nullptr, h.t, h.s, h.t, 1, FIN_OMEGA, true, s);
+  k_bicg_xr<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.xi, h.ph, h.sh, h.s, h.t, h.r, h.rhat, h.red, 2);
+  GBS_LAUNCH_CHECK();
+}
+
+void run_iteration(Handle& h, bool tr, cudaStream_t s) {
+  if (!h.prm.use_graph) {
+    bicg_iteration(h, tr, s);
+    return;
+  }
+  cudaGraphExec_t& ge = h.gexec[tr ? 1 : 0];
+  if (!ge) {
+    cudaGraph_t g = nullptr;
+    GBS_CUDA(cudaStreamBeginCapture(h.cap, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = launch_count();
+    try {
+      bicg_iteration(h, tr, h.cap);
+    } catch (...) {
+      cudaStreamEndCapture(h.cap, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    h.gnodes[tr ? 1 : 0] = launch_count() - before;
+    count_launch(-(launch_count() - before));  // captured, not executed
+    GBS_CUDA(cudaStreamEndCapture(h.cap, &g));
+    cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      ge = nullptr;
+      throw CudaError{std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)};
+    }
+  }
+  GBS_CUDA(cudaGraphLaunch(ge, s));
+  count_launch(h.gnodes[tr ? 1 : 0]);
+}
+
+gbs_status finish(Handle& h, gbs_info* info, int iters, int repl, double rel, bool conv,
+                  std::vector<double>& hist, cudaStream_t s) {
+  GBS_CUDA(cudaEventRecord(h.ev1, s));
+  GBS_CUDA(cudaEventSynchronize(h.ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h.ev0, h.ev1);
+  if (info) {
+    info->iters = iters;
+    info->replacements = repl;
+    info->converged = conv ? 1 : 0;
+    info->rel_res = rel;
+    info->ms = ms;
+    info->history_len = 0;
+    if (info->history && info->history_cap > 0) {
+      int nh = std::min<int>(info->history_cap, (int)hist.size());
+      std::memcpy(info->history, hist.data(), sizeof(double) * nh);
+      info->history_len = nh;
+    }
+  }
+  if (!std::isfinite(rel)) {
+    g_err = "NaN or Inf in the residual norm";
+    return GBS_ERR_NAN;
+  }
+  return conv ? GBS_OK : GBS_NOT_CONVERGED;
+}
+
+gbs_status solve_bicgstab(Handle& h, const double* b, double* x, bool tr, cudaStream_t s,
+                          gbs_info* info) {
+  const int64_t n = h.n;
+  std::vector<double> hist;
+  GBS_CUDA(cudaEventRecord(h.ev0, s));
+  GBS_CUDA(cudaMemcpyAsync(h.bi, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GBS_CUDA(cudaMemcpyAsync(h.xi, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
+  GBS_LAUNCH_CHECK();
+  outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, h.r, 4, FIN_INIT, true, s);
+  GBS_CUDA(cudaMemcpyAsync(h.rhat, h.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  read_scalars(h, s);
+  const double bb = h.sc_host[S_BB];
+  if (!std::isfinite(bb)) {
+    g_err = "NaN or Inf in b";
+    return GBS_ERR_NAN;
+  }
+  if (bb == 0.0) {
+    GBS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    return finish(h, info, 0, 0, 0.0, true, hist, s);
+  }
+  const double nb = std::sqrt(bb);
+  double rel = std::sqrt(h.sc_host[S_RR]) / nb;
+  int it = 0, repl = 0;
+  bool conv = rel <= h.prm.tol;
+  bool breakdown = false;
+  while (!conv && it < h.prm.maxiter) {
+    ++it;
+    run_iteration(h, tr, s);
+    read_scalars(h, s);
+    const double* c = h.sc_host;
+    if (c[S_BREAK] != 0.0) {
+      breakdown = true;
+      break;
+    }
+    double res = std::sqrt(c[S_RR]) / nb;
+    if (!std::isfinite(res)) {
+      rel = res;
+      break;
+    }
+    hist.push_back(res);
+    const bool claim = res <= h.prm.tol;
+    if (claim || it % h.prm.replace_every == 0) {
+      outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, h.rhat, h.r, 4, FIN_REPLACE, true, s);
+      read_scalars(h, s);
+      ++repl;
+      rel = std::sqrt(h.sc_host[S_RR]) / nb;
+      if (rel <= h.prm.tol) {
+        conv = true;
+        break;
+      }
+      if (claim) {
+        GBS_CUDA(cudaMemcpyAsync(h.rhat, h.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        k_set_restart<<<1, 1, 0, s>>>(h.sc);
+        GBS_LAUNCH_CHECK();
+      }
+      if (h.sc_host[S_OMEGA] == 0.0 && !claim) {
+        breakdown = true;
+        break;
+      }
+    } else if (c[S_OMEGA] == 0.0 || c[S_RHO] == 0.0) {
+      breakdown = true;
+      break;
+    }
+  }
+  if (!conv) {
+    outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, h.r, 4, FIN_RR, true, s);
+    read_scalars(h, s);
+    rel = std::sqrt(h.sc_host[S_RR]) / nb;
+    conv = rel <= h.prm.tol;
+  }
+  GBS_CUDA(cudaMemcpyAsync(x, h.xi, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  gbs_status st = finish(h, info, it, repl, rel, conv, hist, s);
+  if (breakdown && !conv && st == GBS_NOT_CONVERGED) {
+    g_err = "BiCGStab breakdown";
+    return GBS_ERR_BREAKDOWN;
+  }
+  return st;
+}
+
+void givens(double a, double b, double& c, double& sn) {
+  if (b == 0.0) {
+    c = 1.0;
+    sn = 0.0;
+    return;
+  }
+  double r = std::hypot(a, b);
+  c = a / r;
+  sn = b / r;
+}
+
+gbs_status solve_gmres(Handle& h, const double* b, double* x, bool tr, cudaStream_t s,
+                       gbs_info* info) {
+  const int64_t n = h.n;
+  const int m = h.m;
+  const unsigned g = vgrid(n);
+  std::vector<double> hist;
+  GBS_CUDA(cudaEventRecord(h.ev0, s));
+  GBS_CUDA(cudaMemcpyAsync(h.bi, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GBS_CUDA(cudaMemcpyAsync(h.xi, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
+  GBS_LAUNCH_CHECK();
+  read_scalars(h, s);
+  const double bb = h.sc_host[S_BB];
+  if (!std::isfinite(bb)) {
+    g_err = "NaN or Inf in b";
+    return GBS_ERR_NAN;
+  }
+  if (bb == 0.0) {
+    GBS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    return finish(h, info, 0, 0, 0.0, true, hist, s);
+  }
+  const double nb = std::sqrt(bb);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  int it = 0, repl = 0;
+  double rel = INFINITY;
+  bool conv = false;
+  for (;;) {
+    outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, h.r, 4, FIN_RR, true, s);
+    read_scalars(h, s);
+    ++repl;
+    const double beta = std::sqrt(h.sc_host[S_RR]);
+    rel = beta / nb;
+    if (!std::isfinite(rel)) break;
+    if (rel <= h.prm.tol) {
+      conv = true;
+      break;
+    }
+    if (it >= h.prm.maxiter) break;
+    k_scale_rr<<<g, 256, 0, s>>>(n, h.r, h.V, h.sc);
+    GBS_LAUNCH_CHECK();
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int j = 0;
+    while (j < m && it < h.prm.maxiter) {
+      double* w = h.V + (size_t)(j + 1) * n;
+      h.pc->apply(h.V + (size_t)j * n, h.z, tr, s);
+      outer(h, tr, SPMV_SET, h.z, nullptr, w, nullptr, nullptr, 0, FIN_STORE, false, s);
+      const int J = j + 1;
+      k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol, h.red, 5, nullptr);
+      GBS_LAUNCH_CHECK();
+      k_orth<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol, nullptr, h.red, 6, nullptr);
+      GBS_LAUNCH_CHECK();
+      const double* gate = h.sc + S_REORTH;
+      k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol2, h.red, 7, gate);
+      GBS_LAUNCH_CHECK();
+      k_orth<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol2, h.hcol, h.red, 8, gate);
+      GBS_LAUNCH_CHECK();
+      k_normalize<<<g, 256, 0, s>>>(n, w, h.sc, h.hcol + J);
+      GBS_LAUNCH_CHECK();
+      GBS_CUDA(cudaMemcpyAsync(h.h_host, h.hcol, sizeof(double) * (J + 1), cudaMemcpyDeviceToHost, s));
+      GBS_CUDA(cudaStreamSynchronize(s));
+      for (int i = 0; i <= J; ++i) H[(size_t)i * m + j] = h.h_host[i];
+      for (int i = 0; i < j; ++i) {
+        double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      givens(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j], cs[j], sn[j]);
+      H[(size_t)j * m + j] = cs[j] * H[(size_t)j * m + j] + sn[j] * H[(size_t)(j + 1) * m + j];
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      ++it;
+      ++j;
+      double est = std::fabs(gv[j]) / nb;
+      hist.push_back(est);
+      if (!std::isfinite(est) || est <= h.prm.tol) break;
+    }
+    for (int i = j - 1; i >= 0; --i) {
+      double acc = gv[i];
+      for (int k = i + 1; k < j; ++k) acc -= H[(size_t)i * m + k] * y[k];
+      y[i] = acc / H[(size_t)i * m + i];
+    }
+    GBS_CUDA(cudaMemcpyAsync(h.ydev, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
+    k_combine<<<g, 256, 0, s>>>(n, h.V, j, h.ydev, h.u);
+    GBS_LAUNCH_CHECK();
+    h.pc->apply(h.u, h.z, tr, s);
+    k_axpy<<<g, 256, 0, s>>>(n, 1.0, h.z, h.xi);
+    GBS_LAUNCH_CHECK();
+    GBS_CUDA(cudaStreamSynchronize(s));  // y is a pageable host buffer
+  }
+  GBS_CUDA(cudaMemcpyAsync(x, h.xi, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  return finish(h, info, it, repl, rel, conv, hist, s);
+}
+
+void need_aligned(const void* p, const char* what) {
+  if (reinterpret_cast<uintptr_t>(p) % 16 != 0)
+    throw SetupError{std::string(what) + " is not 16-byte aligned"};
+}
+
+void need_device(const Handle& h) {
+  if (!h.pc) throw SetupError{"hierarchy was built with setup_only (no device data)"};
+}
+
+gbs_status solve(Handle& h, const double* b, double* x, bool tr, cudaStream_t s, gbs_info* info) {
+  need_device(h);
+  if (!b || !x) throw SetupError{"null vector"};
+  need_aligned(b, "b");
+  need_aligned(x, "x");
+  if (tr && !h.prm.enable_adjoint) throw SetupError{"hierarchy was built without enable_adjoint"};
+  if (h.prm.krylov == GBS_GMRES) return solve_gmres(h, b, x, tr, s, info);
+  return solve_bicgstab(h, b, x, tr, s, info);
+}
+
+void init_device() {
+  int nd = 0;
+  cudaError_t e = cudaGetDeviceCount(&nd);
+  if (e != cudaSuccess || nd == 0)
+    throw CudaError{std::string("no CUDA device: ") + cudaGetErrorString(e)};
+}
+
+void finish_build(Handle& h, cudaStream_t s) {
+  PrecondOptions o = pc_opts(&h.prm);
+  if (h.schur) h.pc = make_schur_precond(h.Sh, h.HA, h.HS, o, s);
+  else h.pc = make_amg_precond(h.H, o, s);
+  alloc_work(h, s);
+}
+
+template <class F>
+gbs_status guarded(F&& f) {
+  try {
+    g_err.clear();
+    return f();
+  } catch (const SetupError& e) {
+    g_err = e.msg;
+    return GBS_ERR_INVALID;
+  } catch (const CudaError& e) {
+    g_err = e.msg;
+    return e.msg.find("cudaMalloc") != std::string::npos ? GBS_ERR_OOM : GBS_ERR_CUDA;
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return GBS_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return GBS_ERR_INVALID;
+  }
+}
+
+}  // namespace
+
+std::unique_ptr<DevPrecond> make_amg_precond(const HAmg& H, const PrecondOptions& o,
+                                             cudaStream_t s) {
+  switch (o.precision) {
+    case 1: return make_amg_fp32(H, o, s);
+    case 2: return make_amg_bf16(H, o, s);
+    default: return make_amg_fp64(H, o, s);
+  }
+}
+std::unique_ptr<DevPrecond> make_schur_precond(const HSchur& Sc, const HAmg& HA, const HAmg& HS,
+                                               const PrecondOptions& o, cudaStream_t s) {
+  switch (o.precision) {
+    case 1: return make_schur_fp32(Sc, HA, HS, o, s);
+    case 2: return make_schur_bf16(Sc, HA, HS, o, s);
+    default: return make_schur_fp64(Sc, HA, HS, o, s);
+  }
+}
+
+}  // namespace gbs
+
+using namespace gbs;
+
+struct gbs_hierarchy {
+  Handle h;
+};
+
+extern "C" {
+
+const char* gbs_last_error(void) { return g_err.c_str(); }
+
+int64_t gbs_kernel_launches(void) { return launch_count(); }
+
+gbs_status gbs_params_default(gbs_params* p) {
+  if (!p) {
+    g_err = "null params";
+    return GBS_ERR_INVALID;
+  }
+  std::memset(p, 0, sizeof(*p));
+  p->precond = GBS_PC_AMG;
+  p->krylov = GBS_BICGSTAB;
+  p->restart = 30;
+  p->tol = 1e-8;
+  p->maxiter = 1000;
+  p->replace_every = 50;
+  p->precision = GBS_FP64;
+  p->eps_strong = 0.08;
+  p->coarse_enough = 1000;
+  p->max_levels = 10;
+  p->npre = 1;
+  p->npost = 1;
+  p->relax = GBS_SPAI0;
+  p->relax_p = GBS_SPAI0;
+  p->jacobi_omega = 0.72;
+  p->smooth_P = 1;
+  p->power_iters = 20;
+  p->nvel = 3;
+  p->use_graph = 1;
+  p->enable_adjoint = 1;
+  p->setup_only = 0;
+  return GBS_OK;
+}
+
+gbs_status gbs_build_hierarchy(const gbs_bsr* A, const gbs_params* params, void* stream,
+                               gbs_hierarchy** out) {
+  return guarded([&]() -> gbs_status {
+    if (!out) throw SetupError{"null output handle"};
+    *out = nullptr;
+    check_params(params);
+    HBsr K = from_c(A);
+    validate(K, true);
+    if (!params->setup_only) init_device();
+    auto hh = std::make_unique<gbs_hierarchy>();
+    Handle& h = hh->h;
+    h.prm = *params;
+    h.B = K.br;
+    h.n = (int64_t)K.nbr * K.br;
+    if (params->precond == GBS_PC_SCHUR) {
+      h.schur = true;
+      if (K.br != params->nvel + 1) throw SetupError{"Schur needs bdim = nvel + 1"};
+      h.Sh = schur_split(K, params->nvel);
+      h.HA = build_amg(h.Sh.A, amg_prm(params, params->relax));
+      h.HS = build_amg(h.Sh.S, amg_prm(params, params->relax_p));
+    } else {
+      h.H = build_amg(K, amg_prm(params, params->relax));
+    }
+    h.Kh = std::move(K);
+    if (!params->setup_only) finish_build(h, S(stream));
+    *out = hh.release();
+    return GBS_OK;
+  });
+}
+
+gbs_status gbs_import_hierarchy(const gbs_bsr* A, const gbs_bsr* P, const gbs_bsr* R,
+                                const double* const* M, const double* Ainv, int32_t nlev,
+                                const gbs_params* params, void* stream, gbs_hierarchy** out) {
+  return guarded([&]() -> gbs_status {
+    if (!out) throw SetupError{"null output handle"};
+    *out = nullptr;
+    check_params(params);
+    if (params->precond != GBS_PC_AMG) throw SetupError{"import supports the AMG preconditioner"};
+    if (nlev < 1 || !A || !Ainv || (nlev > 1 && (!P || !R || !M)))
+      throw SetupError{"bad level arrays"};
+    init_device();
+    auto hh = std::make_unique<gbs_hierarchy>();
+    Handle& h = hh->h;
+    h.prm = *params;
+    HBsr K = from_c(&A[0]);
+    validate(K, true);
+    h.B = K.br;
+    h.n = (int64_t)K.nbr * K.br;
+    HAmg& H = h.H;
+    H.B = K.br;
+    for (int l = 0; l + 1 < nlev; ++l) {
+      HLevel L;
+      L.A = from_c(&A[l]);
+      L.P = from_c(&P[l]);
+      L.R = from_c(&R[l]);
+      validate(L.A, true);
+      validate(L.P, false);
+      validate(L.R, false);
+      HBsr An = from_c(&A[l + 1]);
+      if (L.A.br != H.B || L.P.br != H.B || L.R.br != H.B || An.br != H.B)
+        throw SetupError{"all levels need the same bdim"};
+      if (L.P.nbr != L.A.nbr || L.P.nbc != An.nbr || L.R.nbr != An.nbr || L.R.nbc != L.A.nbr)
+        throw SetupError{"level " + std::to_string(l) + ": P/R shapes do not match A"};
+      if (!M[l]) throw SetupError{"null smoother blocks"};
+      L.M.assign(M[l], M[l] + (size_t)L.A.nbr * H.B * H.B);
+      H.levels.push_back(std::move(L));
+    }
+    H.Ac = from_c(&A[nlev - 1]);
+    validate(H.Ac, true);
+    const size_t nc = (size_t)H.Ac.nbr * H.B;
+    if (nc > 8192) throw SetupError{"coarsest level too large for a dense inverse"};
+    H.Ainv.assign(Ainv, Ainv + nc * nc);
+    h.Kh = std::move(K);
+    if (params->setup_only) throw SetupError{"import needs device upload (setup_only = 0)"};
+    finish_build(h, S(stream));
+    *out = hh.release();
+    return GBS_OK;
+  });
+}
+
+gbs_status gbs_solve(gbs_hierarchy* hh, const double* b, double* x, void* stream, gbs_info* info) {
+  return guarded([&]() -> gbs_status {
+    if (!hh) throw SetupError{"null handle"};
+    return solve(hh->h, b, x, false, S(stream), info);
+  });
+}
+
+gbs_status gbs_solve_adjoint(gbs_hierarchy* hh, const double* g, double* lam, void* stream,
+                             gbs_info* info) {
+  return guarded([&]() -> gbs_status {
+    if (!hh) throw SetupError{"null handle"};
+    return solve(hh->h, g, lam, true, S(stream), info);
+  });
+}
+
+gbs_status gbs_sampled_outer(const gbs_hierarchy* hh, const double* lam, const double* x,
+                             double alpha, double* grad, void* stream) {
+  return guarded([&]() -> gbs_status {
+    if (!hh || !lam || !x || !grad) throw SetupError{"null argument"};
+    const Handle& h = hh->h;
+    need_device(h);
+    need_aligned(lam, "lam");
+    need_aligned(x, "x");
+    need_aligned(grad, "grad");
+    cudaStream_t s = S(stream);
+#define GBS_SO(BB)                                                                    \
+  k_sampled_outer<BB><<<grid_for(row_threads<BB>(h.K.nbr)), 256, 0, s>>>(h.K, lam, x, \
+                                                                         alpha, grad)
+    switch (h.B) {
+      case 1: GBS_SO(1); break;
+      case 2: GBS_SO(2); break;
+      case 3: GBS_SO(3); break;
+      case 4: GBS_SO(4); break;
+    }
+#undef GBS_SO
+    GBS_LAUNCH_CHECK();
+    return GBS_OK;
+  });
+}
+
+gbs_status gbs_update_values(gbs_hierarchy* hh, const double* vals, void* stream) {
+  return guarded([&]() -> gbs_status {
+    if (!hh || !vals) throw SetupError{"null argument"};
+    Handle& h = hh->h;
+    need_device(h);
+    need_aligned(vals, "vals");
+    GBS_CUDA(cudaMemcpyAsync(h.Kval, vals, sizeof(double) * h.Kh.val.size(),
+                             cudaMemcpyDeviceToDevice, S(stream)));
+    return GBS_OK;
+  });
+}
+
+gbs_status gbs_spmv(const gbs_hierarchy* hh, const double* x, double* y, int32_t transpose,
+                    void* stream) {
+  return guarded([&]() -> gbs_status {
+    if (!hh || !x || !y) throw SetupError{"null argument"};
+    const Handle& h = hh->h;
+    need_device(h);
+    need_aligned(x, "x");
+    need_aligned(y, "y");
+    if (transpose && !h.K.tmap) throw SetupError{"built without enable_adjoint"};
+    outer(h, transpose != 0, SPMV_SET, x, nullptr, y, nullptr, nullptr, 0, FIN_STORE, false,
+          S(stream));
+    return GBS_OK;
+  });
+}
+
+gbs_status gbs_apply_precond(gbs_hierarchy* hh, const double* r, double* z, int32_t transpose,
+                             void* stream) {
+  return guarded([&]() -> gbs_status {
+    if (!hh || !r || !z) throw SetupError{"null argument"};
+    Handle& h = hh->h;
+    need_device(h);
+    need_aligned(r, "r");
+    need_aligned(z, "z");
+    if (transpose && !h.prm.enable_adjoint) throw SetupError{"built without enable_adjoint"};
+    h.pc->apply(r, z, transpose != 0, S(stream));
+    return GBS_OK;
+  });
+}
+
+gbs_status gbs_hierarchy_info(const gbs_hierarchy* hh, int32_t which, int32_t* nlevels,
+                              int32_t* n_brows, int64_t* nnzb, int32_t cap, int64_t* bytes) {
+  return guarded([&]() -> gbs_status {
+    if (!hh || !nlevels) throw SetupError{"null argument"};
+    const Handle& h = hh->h;
+    if (which < 0 || which > 1 || (which == 1 && !h.schur)) throw SetupError{"bad hierarchy id"};
+    const HAmg& H = h.schur ? (which == 0 ? h.HA : h.HS) : h.H;
+    const int nl = (int)H.levels.size() + 1;
+    *nlevels = nl;
+    for (int l = 0; l < nl && l < cap; ++l) {
+      const HBsr& A = l + 1 == nl ? H.Ac : H.levels[l].A;
+      if (n_brows) n_brows[l] = A.nbr;
+      if (nnzb) nnzb[l] = A.nnzb();
+    }
+    if (bytes) *bytes = h.pc ? h.pc->bytes() + h.ar.bytes : 0;
+    return GBS_OK;
+  });
+}
+
+gbs_status gbs_export_level(const gbs_hierarchy* hh, int32_t which, int32_t level, int32_t part,
+                            int32_t* n_brows, int32_t* n_bcols, int64_t* nnzb, int32_t* row_ptr,
+                            int32_t* col_idx, double* vals) {
+  return guarded([&]() -> gbs_status {
+    if (!hh || !n_brows || !n_bcols || !nnzb) throw SetupError{"null argument"};
+    const Handle& h = hh->h;
+    if (which < 0 || which > 1 || (which == 1 && !h.schur)) throw SetupError{"bad hierarchy id"};
+    const HAmg& H = h.schur ? (which == 0 ? h.HA : h.HS) : h.H;
+    const int nl = (int)H.levels.size() + 1;
+    if (level < 0 || level >= nl) throw SetupError{"bad level"};
+    const bool coarsest = level == nl - 1;
+    const HBsr* M = nullptr;
+    if (part == 0) M = coarsest ? &H.Ac : &H.levels[level].A;
+    else if (part == 1 || part == 2) {
+      if (coarsest) throw SetupError{"the coarsest level has no P/R"};
+      M = part == 1 ? &H.levels[level].P : &H.levels[level].R;
+    }
+    if (M) {
+      *n_brows = M->nbr;
+      *n_bcols = M->nbc;
+      *nnzb = M->nnzb();
+      if (row_ptr) std::memcpy(row_ptr, M->ptr.data(), sizeof(int32_t) * M->ptr.size());
+      if (col_idx) std::memcpy(col_idx, M->col.data(), sizeof(int32_t) * M->col.size());
+      if (vals) std::memcpy(vals, M->val.data(), sizeof(double) * M->val.size());
+      return GBS_OK;
+    }
+    if (part == 3 || part == 4) {
+      if (coarsest) throw SetupError{"the coarsest level has no smoother/aggregates"};
+      const HLevel& L = H.levels[level];
+      *n_brows = L.A.nbr;
+      *n_bcols = part == 3 ? H.B : 1;
+      *nnzb = 0;
+      if (part == 3 && vals) std::memcpy(vals, L.M.data(), sizeof(double) * L.M.size());
+      if (part == 4 && col_idx) std::memcpy(col_idx, L.agg.data(), sizeof(int32_t) * L.agg.size());
+      return GBS_OK;
+    }
+    if (part == 5) {
+      if (!coarsest) throw SetupError{"the dense inverse lives on the coarsest level"};
+      *n_brows = H.Ac.nbr * H.B;
+      *n_bcols = H.Ac.nbr * H.B;
+      *nnzb = 0;
+      if (vals) std::memcpy(vals, H.Ainv.data(), sizeof(double) * H.Ainv.size());
+      return GBS_OK;
+    }
+    throw SetupError{"bad part"};
+  });
+}
+
+gbs_status gbs_destroy(gbs_hierarchy* hh) {
+  return guarded([&]() -> gbs_status {
+    if (!hh) return GBS_OK;
+    if (hh->h.pc) cudaDeviceSynchronize();
+    delete hh;
+    return GBS_OK;
+  });
+}
+
+}  // extern "C"

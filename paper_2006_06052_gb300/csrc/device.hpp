@@ -1,0 +1,102 @@
+// Device-resident preconditioners (internal interface).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "setup.hpp"
+
+namespace gbs {
+
+struct CudaError {
+  std::string msg;
+};
+
+#define GBS_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e__ = (call);                                                       \
+    if (e__ != cudaSuccess)                                                         \
+      throw ::gbs::CudaError{std::string(#call) + ": " + cudaGetErrorString(e__)};  \
+  } while (0)
+
+// Kernel launches issued by this library (see gbs_kernel_launches).
+void count_launch(int64_t k = 1);
+int64_t launch_count();
+
+#define GBS_LAUNCH_CHECK()               \
+  do {                                   \
+    GBS_CUDA(cudaPeekAtLastError());     \
+    ::gbs::count_launch();               \
+  } while (0)
+
+// Owns device allocations; counts bytes.
+struct Arena {
+  std::vector<void*> ptrs;
+  int64_t bytes = 0;
+  template <class T>
+  T* alloc(size_t n) {
+    if (n == 0) n = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw CudaError{"cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed: " +
+                      cudaGetErrorString(e)};
+    }
+    ptrs.push_back(p);
+    bytes += (int64_t)(n * sizeof(T));
+    return static_cast<T*>(p);
+  }
+  template <class T>
+  T* upload(const T* h, size_t n, cudaStream_t s) {
+    T* d = alloc<T>(n);
+    if (n) GBS_CUDA(cudaMemcpyAsync(d, h, n * sizeof(T), cudaMemcpyHostToDevice, s));
+    return d;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+  ~Arena() { release(); }
+};
+
+// A preconditioner z = M^-1 r acting on FP64 outer vectors.
+struct DevPrecond {
+  virtual ~DevPrecond() = default;
+  virtual void apply(const double* r, double* z, bool transpose, cudaStream_t s) = 0;
+  virtual int64_t bytes() const = 0;
+  virtual int nlevels(int which) const = 0;
+  virtual int64_t level_rows(int which, int l) const = 0;
+  virtual int64_t level_nnzb(int which, int l) const = 0;
+  // algorithmic bytes moved by one application (from the stored sizes)
+  virtual double bytes_per_apply() const = 0;
+};
+
+struct PrecondOptions {
+  int precision = 0;   // 0 FP64, 1 FP32, 2 BF16
+  int npre = 1, npost = 1;
+  bool tmaps = true;
+};
+
+std::unique_ptr<DevPrecond> make_amg_precond(const HAmg& H, const PrecondOptions& o,
+                                             cudaStream_t s);
+std::unique_ptr<DevPrecond> make_schur_precond(const HSchur& S, const HAmg& HA, const HAmg& HS,
+                                               const PrecondOptions& o, cudaStream_t s);
+
+// Per-form factories (one translation unit each).
+std::unique_ptr<DevPrecond> make_amg_fp64(const HAmg&, const PrecondOptions&, cudaStream_t);
+std::unique_ptr<DevPrecond> make_amg_fp32(const HAmg&, const PrecondOptions&, cudaStream_t);
+std::unique_ptr<DevPrecond> make_amg_bf16(const HAmg&, const PrecondOptions&, cudaStream_t);
+std::unique_ptr<DevPrecond> make_schur_fp64(const HSchur&, const HAmg&, const HAmg&,
+                                            const PrecondOptions&, cudaStream_t);
+std::unique_ptr<DevPrecond> make_schur_fp32(const HSchur&, const HAmg&, const HAmg&,
+                                            const PrecondOptions&, cudaStream_t);
+std::unique_ptr<DevPrecond> make_schur_bf16(const HSchur&, const HAmg&, const HAmg&,
+                                            const PrecondOptions&, cudaStream_t);
+
+}  // namespace gbs

@@ -1,0 +1,390 @@
+// FP64 outer-Krylov kernels: SpMV of K with fused dot products,
+// BiCGStab vector updates, GMRES orthogonalisation, sampled outer
+// product.  Dots use a deterministic two-level reduction: a fixed grid of
+// RED_BLOCKS blocks, warp-shuffle + shared-memory tree per block, then
+// the last block to finish sums the per-block partials in block order
+// and runs a scalar epilogue ("finalize") on thread 0.  No result depends
+// on block scheduling.
+//
+// Scalars of the iteration live in device memory (sc[]), so kernels read
+// alpha, beta, omega there and only the convergence check crosses to the
+// host (Section 2.3's residual and inner-product primitives, kept in FP64
+// as in the mixed-precision scheme of Section 4, Listing V4).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace gbs {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS = 152 * 4;
+constexpr int MAX_DOTS = 72;   // GMRES multi-dot: up to 64 basis vectors + spares
+
+enum ScalarSlot {
+  S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_RV, S_TS, S_TT, S_RR, S_BB, S_FIRST, S_BREAK,
+  S_WW0, S_WW, S_REORTH, S_D0, S_D1, S_COUNT = 32
+};
+
+enum FinOp {
+  FIN_STORE = 0,   // sc[S_D0] = d0, sc[S_D1] = d1
+  FIN_ALPHA,       // rv = d0; alpha = rho / rv
+  FIN_OMEGA,       // ts = d0, tt = d1, omega = ts / tt
+  FIN_RHO,         // rho_old = rho; rho = d0; rr = d1; first = 0
+  FIN_REPLACE,     // rho = d0; rr = d1
+  FIN_INIT,        // rhat = r: rho = rr = d1; rho_old = alpha = omega = 1; first = 1
+  FIN_BB,          // bb = d0
+  FIN_RR           // rr = d1
+};
+
+struct Red {
+  double* partials;   // RED_BLOCKS * MAX_DOTS
+  unsigned* counter;  // one per reduction slot; reset by the last block
+  double* sc;
+};
+
+__device__ __forceinline__ void finalize(int op, const double* d, double* sc) {
+  switch (op) {
+    case FIN_STORE: sc[S_D0] = d[0]; sc[S_D1] = d[1]; break;
+    case FIN_ALPHA:
+      sc[S_RV] = d[0];
+      if (d[0] == 0.0 || !isfinite(d[0])) { sc[S_BREAK] = 1.0; sc[S_ALPHA] = 0.0; }
+      else sc[S_ALPHA] = sc[S_RHO] / d[0];
+      break;
+    case FIN_OMEGA:
+      sc[S_TS] = d[0];
+      sc[S_TT] = d[1];
+      sc[S_OMEGA] = d[1] > 0.0 ? d[0] / d[1] : 0.0;
+      break;
+    case FIN_RHO:
+      sc[S_RHO_OLD] = sc[S_RHO];
+      sc[S_RHO] = d[0];
+      sc[S_RR] = d[1];
+      sc[S_FIRST] = 0.0;
+      break;
+    case FIN_REPLACE: sc[S_RHO] = d[0]; sc[S_RR] = d[1]; break;
+    case FIN_INIT:
+      sc[S_RHO] = d[1];
+      sc[S_RR] = d[1];
+      sc[S_RHO_OLD] = 1.0;
+      sc[S_ALPHA] = 1.0;
+      sc[S_OMEGA] = 1.0;
+      sc[S_FIRST] = 1.0;
+      sc[S_BREAK] = 0.0;
+      break;
+    case FIN_BB: sc[S_BB] = d[0]; break;
+    case FIN_RR: sc[S_RR] = d[1]; break;
+  }
+}
+
+// Block-level deterministic reduction of ND values held per thread; the
+// result is valid in thread 0.
+template <int ND>
+__device__ __forceinline__ void block_sum(double (&v)[ND], double (*sh)[ND]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < ND; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < ND; ++q) sh[w][q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      double s = 0.0;
+      for (int i = 0; i < nw; ++i) s += sh[i][q];
+      v[q] = s;
+    }
+  }
+}
+
+// Store the block partials, and in the last block reduce them and run
+// the epilogue.  Returns true in the thread that ran the epilogue.
+template <int ND>
+__device__ __forceinline__ void grid_reduce(double (&v)[ND], const Red& R, int slot, int op) {
+  __shared__ double sh[RED_THREADS / 32][ND];
+  __shared__ bool last;
+  block_sum<ND>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < ND; ++q) R.partials[(size_t)blockIdx.x * ND + q] = v[q];
+    __threadfence();
+    unsigned t = atomicAdd(R.counter + slot, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s[ND];
+#pragma unroll
+  for (int q = 0; q < ND; ++q) s[q] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < ND; ++q) s[q] += __ldcg(R.partials + (size_t)b * ND + q);
+  }
+  block_sum<ND>(s, sh);
+  if (threadIdx.x == 0) {
+    double d[2] = {s[0], ND > 1 ? s[ND > 1 ? 1 : 0] : 0.0};
+    finalize(op, d, R.sc);
+    R.counter[slot] = 0u;
+  }
+}
+
+// y = K x (RESID: y = f - K x); d0 = sum y*w0, d1 = sum y*w1 (null w: 0).
+template <int B, bool TR, int MODE>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_outer(DevBsr<double> K, const double* __restrict__ x, const double* __restrict__ f,
+            double* __restrict__ y, const double* __restrict__ w0, const double* __restrict__ w1,
+            Red R, int slot, int op, int reduce) {
+  constexpr int RPW = 32 / B;
+  double d[2] = {0.0, 0.0};
+  const int64_t nwarps = ((int64_t)K.nbr + RPW - 1) / RPW;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / B, r = lane - sub * B;
+  const bool lane_ok = sub < RPW;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < nwarps;
+       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int brow = (int)(w * RPW + sub);
+    if (!lane_ok || brow >= K.nbr) continue;
+    double acc = row_dot<B, TR, double, double, double>(K, x, brow, r);
+    const size_t o = (size_t)brow * B + r;
+    double val = MODE == SPMV_RESID ? f[o] - acc : acc;
+    y[o] = val;
+    if (w0) d[0] += val * w0[o];
+    if (w1) d[1] += val * w1[o];
+  }
+  if (reduce) grid_reduce<2>(d, R, slot, op);
+}
+
+// p = r + beta (p - omega v), beta = (rho / rho_old) (alpha / omega); p = r on the first step.
+__global__ void k_bicg_p(int64_t n, const double* __restrict__ r, const double* __restrict__ v,
+                         double* __restrict__ p, const double* __restrict__ sc) {
+  const bool first = sc[S_FIRST] != 0.0;
+  const double omega = sc[S_OMEGA];
+  const double beta = first ? 0.0 : (sc[S_RHO] / sc[S_RHO_OLD]) * (sc[S_ALPHA] / omega);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = first ? r[i] : r[i] + beta * (p[i] - omega * v[i]);
+}
+
+// s = r - alpha v
+__global__ void k_bicg_s(int64_t n, const double* __restrict__ r, const double* __restrict__ v,
+                         double* __restrict__ s, const double* __restrict__ sc) {
+  const double alpha = sc[S_ALPHA];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s[i] = r[i] - alpha * v[i];
+}
+
+// x += alpha phat + omega shat; r = s - omega t; d0 = rhat.r, d1 = r.r
+__global__ void __launch_bounds__(RED_THREADS)
+    k_bicg_xr(int64_t n, double* __restrict__ x, const double* __restrict__ ph,
+              const double* __restrict__ sh, const double* __restrict__ s,
+              const double* __restrict__ t, double* __restrict__ r,
+              const double* __restrict__ rhat, Red R, int slot) {
+  const double alpha = R.sc[S_ALPHA], omega = R.sc[S_OMEGA];
+  double d[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * ph[i] + omega * sh[i];
+    const double ri = s[i] - omega * t[i];
+    r[i] = ri;
+    d[0] += rhat[i] * ri;
+    d[1] += ri * ri;
+  }
+  grid_reduce<2>(d, R, slot, FIN_RHO);
+}
+
+// d0 = a.b, d1 = c.c (c may be null)
+__global__ void __launch_bounds__(RED_THREADS)
+    k_dot2(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+           const double* __restrict__ c, Red R, int slot, int op) {
+  double d[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (a) d[0] += a[i] * b[i];
+    if (c) d[1] += c[i] * c[i];
+  }
+  grid_reduce<2>(d, R, slot, op);
+}
+
+__global__ void k_set_restart(double* sc) {
+  sc[S_RHO] = sc[S_RR];
+  sc[S_RHO_OLD] = 1.0;
+  sc[S_ALPHA] = 1.0;
+  sc[S_OMEGA] = 1.0;
+  sc[S_FIRST] = 1.0;
+}
+
+// ------------------------------------------------------------------ GMRES
+// h[i] = V_i . w for i < J (chunks of 8 vectors), and sc[S_WW0] = w . w.
+// gate: if non-null and *gate == 0 the kernel does nothing.
+__global__ void __launch_bounds__(RED_THREADS)
+    k_multidot(int64_t n, const double* __restrict__ V, int J, const double* __restrict__ w,
+               double* __restrict__ h, Red R, int slot, const double* __restrict__ gate) {
+  if (gate && *gate == 0.0) return;
+  constexpr int CH = 8;
+  __shared__ double sh[RED_THREADS / 32][CH];
+  __shared__ bool last;
+  const int nch = (J + 1 + CH - 1) / CH;  // J dots + w.w
+  for (int c0 = 0; c0 < nch; ++c0) {
+    double v[CH];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) v[q] = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const int vi = c0 * CH + q;
+        if (vi < J) v[q] += V[(size_t)vi * n + i] * wi;
+        else if (vi == J) v[q] += wi * wi;
+      }
+    }
+    block_sum<CH>(v, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < CH; ++q) R.partials[(size_t)blockIdx.x * MAX_DOTS + c0 * CH + q] = v[q];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned t = atomicAdd(R.counter + slot, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int c0 = 0; c0 < nch; ++c0) {
+    double s[CH];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) s[q] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+      for (int q = 0; q < CH; ++q) s[q] += __ldcg(R.partials + (size_t)b * MAX_DOTS + c0 * CH + q);
+    }
+    block_sum<CH>(s, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const int vi = c0 * CH + q;
+        if (vi < J) h[vi] = s[q];
+        else if (vi == J) R.sc[S_WW0] = s[q];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) R.counter[slot] = 0u;
+}
+
+// w -= sum_i h[i] V_i; sc[S_WW] = w.w; sc[S_REORTH] = (ww < 0.5 ww0).
+// accumulate (non-null): hacc[i] += h[i] as well (second pass).
+__global__ void __launch_bounds__(RED_THREADS)
+    k_orth(int64_t n, const double* __restrict__ V, int J, double* __restrict__ w,
+           const double* __restrict__ h, double* __restrict__ hacc, Red R, int slot,
+           const double* __restrict__ gate) {
+  if (gate && *gate == 0.0) return;
+  __shared__ double hs[MAX_DOTS];
+  for (int i = threadIdx.x; i < J; i += blockDim.x) hs[i] = h[i];
+  __syncthreads();
+  double d[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double wi = w[i];
+    for (int q = 0; q < J; ++q) wi -= hs[q] * V[(size_t)q * n + i];
+    w[i] = wi;
+    d[0] += wi * wi;
+  }
+  __shared__ double sh[RED_THREADS / 32][1];
+  __shared__ bool last;
+  block_sum<1>(d, sh);
+  if (threadIdx.x == 0) {
+    R.partials[blockIdx.x] = d[0];
+    __threadfence();
+    unsigned t = atomicAdd(R.counter + slot, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s[1] = {0.0};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s[0] += __ldcg(R.partials + b);
+  block_sum<1>(s, sh);
+  if (threadIdx.x == 0) {
+    R.sc[S_WW] = s[0];
+    if (hacc) {
+      for (int q = 0; q < J; ++q) hacc[q] += hs[q];
+      R.sc[S_REORTH] = 0.0;
+    } else {
+      R.sc[S_REORTH] = (s[0] < 0.5 * R.sc[S_WW0]) ? 1.0 : 0.0;
+    }
+    R.counter[slot] = 0u;
+  }
+}
+
+// w /= sqrt(sc[S_WW]) (if nonzero); hnext = sqrt(sc[S_WW])
+__global__ void k_normalize(int64_t n, double* __restrict__ w, const double* __restrict__ sc,
+                            double* __restrict__ hnext) {
+  const double nrm = sqrt(sc[S_WW]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *hnext = nrm;
+  if (nrm == 0.0) return;
+  const double inv = 1.0 / nrm;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    w[i] *= inv;
+}
+
+// v = r / sqrt(sc[S_RR])
+__global__ void k_scale_rr(int64_t n, const double* __restrict__ r, double* __restrict__ v,
+                           const double* __restrict__ sc) {
+  const double inv = 1.0 / sqrt(sc[S_RR]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = r[i] * inv;
+}
+
+// u = sum_{i<J} y[i] V_i
+__global__ void k_combine(int64_t n, const double* __restrict__ V, int J,
+                          const double* __restrict__ y, double* __restrict__ u) {
+  __shared__ double ys[MAX_DOTS];
+  for (int i = threadIdx.x; i < J; i += blockDim.x) ys[i] = y[i];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < J; ++q) acc += ys[q] * V[(size_t)q * n + i];
+    u[i] = acc;
+  }
+}
+
+__global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+
+// grad[k, a, c] = alpha * lam[B i + a] * x[B j + c] on the stored pattern.
+template <int B>
+__global__ void __launch_bounds__(256)
+    k_sampled_outer(DevBsr<double> K, const double* __restrict__ lam,
+                    const double* __restrict__ x, double alpha, double* __restrict__ grad) {
+  RowMap<B> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  if (!m.lane_ok || m.brow >= K.nbr) return;
+  const double la = alpha * lam[(size_t)m.brow * B + m.r];
+  for (int k = K.rp[m.brow]; k < K.rp[m.brow + 1]; ++k) {
+    const int j = K.col[k];
+    double xv[B];
+    load_run<B, double, double, false>(x + (size_t)j * B, xv);
+    double* g = grad + (size_t)k * (B * B) + m.r * B;
+#pragma unroll
+    for (int c = 0; c < B; ++c) __stcs(g + c, la * xv[c]);
+  }
+}
+
+}  // namespace gbs

@@ -1,0 +1,526 @@
+// Host-side hierarchy construction: smoothed aggregation, SPAI0 /
+// damped Jacobi, Galerkin products, dense coarse inverse, Schur split.
+//
+// Algorithm (the paper composes AMG from smoothed-aggregation coarsening
+// and the SPAI0 smoother, Section 2.1, Listing "composition", with the
+// strong-coupling threshold of Listing "params"; it leaves the inner
+// steps to the AMG literature, so these are the readings used):
+//  - strength: ||A_ij||_F^2 > (eps^2 ||A_ii||_F) ||A_jj||_F, eps halved per
+//    level, squares summed over the block in row-major order;
+//  - greedy aggregation: roots in ascending order when all strong
+//    neighbours are free; leftovers join the pass-1 aggregate of their
+//    strongest neighbour (ties to the smaller aggregate id);
+//  - P = (I - omega D^-1 A) P_tent, omega = 4 / (3 rho(D^-1 A)), rho by
+//    power iteration from x_i = frac(0.6180339887498949 i) - 0.5;
+//  - R = P^T, A_c = R A P;
+//  - SPAI0 (Broker & Grote): M_i = A_ii^T (sum_j A_ij A_ij^T)^-1;
+//    damped Jacobi: M_i = omega A_ii^-1;
+//  - coarsest level: dense LU with partial pivoting, explicit inverse.
+// This translation unit must be compiled with -ffp-contract=off so the
+// strength test rounds like plain IEEE multiply and add.
+#include "setup.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace gbs {
+
+namespace {
+
+[[noreturn]] void fail(const std::string& m) { throw SetupError{m}; }
+
+// C = A * B for B x B blocks (row-major), accumulated into C.
+inline void blk_mul_add(int B, const double* a, const double* b, double* c) {
+  for (int i = 0; i < B; ++i)
+    for (int k = 0; k < B; ++k) {
+      double aik = a[i * B + k];
+      for (int j = 0; j < B; ++j) c[i * B + j] += aik * b[k * B + j];
+    }
+}
+
+// Gauss-Jordan inverse with partial pivoting; false if singular.
+bool blk_inv(int B, const double* a, double* out) {
+  double m[16 * 2];
+  const int W = 2 * B;
+  for (int i = 0; i < B; ++i)
+    for (int j = 0; j < W; ++j) m[i * W + j] = j < B ? a[i * B + j] : (j - B == i ? 1.0 : 0.0);
+  for (int c = 0; c < B; ++c) {
+    int p = c;
+    for (int r = c + 1; r < B; ++r)
+      if (std::fabs(m[r * W + c]) > std::fabs(m[p * W + c])) p = r;
+    if (m[p * W + c] == 0.0) return false;
+    if (p != c)
+      for (int j = 0; j < W; ++j) std::swap(m[p * W + j], m[c * W + j]);
+    double d = m[c * W + c];
+    for (int j = 0; j < W; ++j) m[c * W + j] /= d;
+    for (int r = 0; r < B; ++r) {
+      if (r == c) continue;
+      double f = m[r * W + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < W; ++j) m[r * W + j] -= f * m[c * W + j];
+    }
+  }
+  for (int i = 0; i < B; ++i)
+    for (int j = 0; j < B; ++j) out[i * B + j] = m[i * W + B + j];
+  return true;
+}
+
+int find_col(const HBsr& A, int row, int col) {
+  auto b = A.col.begin() + A.ptr[row];
+  auto e = A.col.begin() + A.ptr[row + 1];
+  auto it = std::lower_bound(b, e, col);
+  if (it != e && *it == col) return (int)(it - A.col.begin());
+  return -1;
+}
+
+std::vector<int> diag_pos(const HBsr& A) {
+  std::vector<int> d(A.nbr);
+  for (int i = 0; i < A.nbr; ++i) {
+    d[i] = find_col(A, i, i);
+    if (d[i] < 0) fail("block row " + std::to_string(i) + " has no stored diagonal block");
+  }
+  return d;
+}
+
+std::vector<double> block_fro2(const HBsr& A) {
+  const int bs = A.bsz();
+  std::vector<double> s(A.nnzb());
+  for (int64_t k = 0; k < A.nnzb(); ++k) {
+    double acc = 0.0;
+    const double* v = &A.val[k * bs];
+    for (int e = 0; e < bs; ++e) acc = acc + v[e] * v[e];
+    s[k] = acc;
+  }
+  return s;
+}
+
+std::vector<double> block_diag_inv(const HBsr& A) {
+  const int B = A.br, bs = B * B;
+  auto d = diag_pos(A);
+  std::vector<double> inv((size_t)A.nbr * bs);
+  for (int i = 0; i < A.nbr; ++i)
+    if (!blk_inv(B, &A.val[(size_t)d[i] * bs], &inv[(size_t)i * bs]))
+      fail("singular diagonal block at row " + std::to_string(i));
+  return inv;
+}
+
+void spmv(const HBsr& A, const std::vector<double>& x, std::vector<double>& y) {
+  const int br = A.br, bc = A.bc, bs = br * bc;
+  y.assign((size_t)A.nbr * br, 0.0);
+  for (int i = 0; i < A.nbr; ++i)
+    for (int a = 0; a < br; ++a) {
+      double acc = 0.0;
+      for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+        const double* v = &A.val[(size_t)k * bs + a * bc];
+        const double* xv = &x[(size_t)A.col[k] * bc];
+        for (int c = 0; c < bc; ++c) acc += v[c] * xv[c];
+      }
+      y[(size_t)i * br + a] = acc;
+    }
+}
+
+double norm2(const std::vector<double>& v) {
+  double s = 0.0;
+  for (double e : v) s += e * e;
+  return std::sqrt(s);
+}
+
+double spectral_radius(const HBsr& A, int iters) {
+  const size_t n = (size_t)A.nbr * A.br;
+  std::vector<double> x(n), y;
+  for (size_t i = 0; i < n; ++i) x[i] = std::fmod((double)i * 0.6180339887498949, 1.0) - 0.5;
+  double nx = norm2(x);
+  for (auto& e : x) e = e / nx;
+  double rho = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    spmv(A, x, y);
+    rho = norm2(y);
+    if (rho == 0.0) break;
+    for (size_t i = 0; i < n; ++i) x[i] = y[i] / rho;
+  }
+  return rho;
+}
+
+HBsr transpose(const HBsr& A) {
+  HBsr T;
+  T.nbr = A.nbc;
+  T.nbc = A.nbr;
+  T.br = A.bc;
+  T.bc = A.br;
+  const int bs = A.bsz();
+  T.ptr.assign(T.nbr + 1, 0);
+  for (auto c : A.col) T.ptr[c + 1]++;
+  for (int i = 0; i < T.nbr; ++i) T.ptr[i + 1] += T.ptr[i];
+  T.col.resize(A.col.size());
+  T.val.resize(A.val.size());
+  std::vector<int32_t> pos(T.ptr.begin(), T.ptr.end() - 1);
+  for (int i = 0; i < A.nbr; ++i)
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      int p = pos[A.col[k]]++;
+      T.col[p] = i;
+      for (int a = 0; a < A.br; ++a)
+        for (int c = 0; c < A.bc; ++c)
+          T.val[(size_t)p * bs + c * A.br + a] = A.val[(size_t)k * bs + a * A.bc + c];
+    }
+  return T;
+}
+
+// C = A * B (square blocks of size Bk), Gustavson row by row.
+HBsr spgemm(const HBsr& A, const HBsr& Bm) {
+  const int B = A.br, bs = B * B;
+  HBsr C;
+  C.nbr = A.nbr;
+  C.nbc = Bm.nbc;
+  C.br = C.bc = B;
+  C.ptr.assign(C.nbr + 1, 0);
+  std::vector<int> mark(C.nbc, -1);
+  std::vector<int> cols;
+  std::vector<double> acc;
+  for (int i = 0; i < A.nbr; ++i) {
+    cols.clear();
+    acc.clear();
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      int j = A.col[k];
+      for (int kk = Bm.ptr[j]; kk < Bm.ptr[j + 1]; ++kk) {
+        int c = Bm.col[kk];
+        if (mark[c] < 0) {
+          mark[c] = (int)cols.size();
+          cols.push_back(c);
+          acc.resize(acc.size() + bs, 0.0);
+        }
+        blk_mul_add(B, &A.val[(size_t)k * bs], &Bm.val[(size_t)kk * bs], &acc[(size_t)mark[c] * bs]);
+      }
+    }
+    std::vector<int> order(cols.size());
+    for (size_t t = 0; t < order.size(); ++t) order[t] = (int)t;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return cols[a] < cols[b]; });
+    for (int t : order) {
+      C.col.push_back(cols[t]);
+      C.val.insert(C.val.end(), acc.begin() + (size_t)t * bs, acc.begin() + (size_t)(t + 1) * bs);
+    }
+    for (int c : cols) mark[c] = -1;
+    C.ptr[i + 1] = (int32_t)C.col.size();
+  }
+  return C;
+}
+
+std::vector<double> dense_inverse(const HBsr& A) {
+  const int B = A.br;
+  const int n = A.nbr * B;
+  std::vector<double> a((size_t)n * n, 0.0);
+  for (int i = 0; i < A.nbr; ++i)
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
+      for (int r = 0; r < B; ++r)
+        for (int c = 0; c < B; ++c)
+          a[(size_t)(i * B + r) * n + A.col[k] * B + c] = A.val[(size_t)k * B * B + r * B + c];
+  // LU with partial pivoting, in place
+  std::vector<int> piv(n);
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(a[(size_t)r * n + c]) > std::fabs(a[(size_t)p * n + c])) p = r;
+    if (a[(size_t)p * n + c] == 0.0) fail("singular coarsest-level matrix");
+    piv[c] = p;
+    if (p != c)
+      for (int j = 0; j < n; ++j) std::swap(a[(size_t)p * n + j], a[(size_t)c * n + j]);
+    double d = a[(size_t)c * n + c];
+    for (int r = c + 1; r < n; ++r) {
+      double f = a[(size_t)r * n + c] / d;
+      a[(size_t)r * n + c] = f;
+      if (f == 0.0) continue;
+      double* rr = &a[(size_t)r * n];
+      const double* cr = &a[(size_t)c * n];
+      for (int j = c + 1; j < n; ++j) rr[j] -= f * cr[j];
+    }
+  }
+  // solve L U X = P I column by column; store X row-major
+  std::vector<double> inv((size_t)n * n), col(n);
+  for (int e = 0; e < n; ++e) {
+    std::fill(col.begin(), col.end(), 0.0);
+    col[e] = 1.0;
+    for (int c = 0; c < n; ++c) std::swap(col[c], col[piv[c]]);
+    for (int r = 0; r < n; ++r) {
+      double s = col[r];
+      for (int j = 0; j < r; ++j) s -= a[(size_t)r * n + j] * col[j];
+      col[r] = s;
+    }
+    for (int r = n - 1; r >= 0; --r) {
+      double s = col[r];
+      for (int j = r + 1; j < n; ++j) s -= a[(size_t)r * n + j] * col[j];
+      col[r] = s / a[(size_t)r * n + r];
+    }
+    for (int r = 0; r < n; ++r) inv[(size_t)r * n + e] = col[r];
+  }
+  return inv;
+}
+
+}  // namespace
+
+void validate(const HBsr& A, bool square) {
+  if (A.nbr < 0 || A.nbc < 0) fail("negative dimension");
+  if (A.br < 1 || A.br > 4 || A.bc < 1 || A.bc > 4) fail("bdim must be in 1..4");
+  if ((int)A.ptr.size() != A.nbr + 1) fail("row_ptr has the wrong length");
+  if (A.ptr[0] != 0) fail("row_ptr[0] != 0");
+  for (int i = 0; i < A.nbr; ++i)
+    if (A.ptr[i + 1] < A.ptr[i]) fail("row_ptr is not monotone at row " + std::to_string(i));
+  if ((int64_t)A.ptr[A.nbr] != A.nnzb()) fail("row_ptr[n] != nnzb");
+  if ((int64_t)A.val.size() != A.nnzb() * A.bsz()) fail("vals has the wrong length");
+  for (int i = 0; i < A.nbr; ++i)
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      if (A.col[k] < 0 || A.col[k] >= A.nbc)
+        fail("column index out of range in row " + std::to_string(i));
+      if (k > A.ptr[i] && A.col[k] <= A.col[k - 1])
+        fail("columns not strictly increasing in row " + std::to_string(i));
+    }
+  for (double v : A.val)
+    if (!std::isfinite(v)) fail("non-finite matrix value");
+  if (square && (A.nbr != A.nbc || A.br != A.bc)) fail("matrix must be square");
+}
+
+std::vector<int32_t> aggregate(const HBsr& A, double eps, int* n_agg_out) {
+  auto s = block_fro2(A);
+  auto dp = diag_pos(A);
+  std::vector<double> d(A.nbr);
+  for (int i = 0; i < A.nbr; ++i) d[i] = std::sqrt(s[dp[i]]);
+  const double e2 = eps * eps;
+  std::vector<char> strong(A.nnzb(), 0);
+  for (int i = 0; i < A.nbr; ++i)
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      int j = A.col[k];
+      if (j == i) continue;
+      double thr = e2 * d[i];
+      strong[k] = s[k] > thr * d[j];
+    }
+  std::vector<int32_t> agg(A.nbr, -1);
+  int n_agg = 0;
+  for (int i = 0; i < A.nbr; ++i) {
+    if (agg[i] != -1) continue;
+    bool free_nb = true;
+    for (int k = A.ptr[i]; k < A.ptr[i + 1] && free_nb; ++k)
+      if (strong[k] && agg[A.col[k]] != -1) free_nb = false;
+    if (!free_nb) continue;
+    agg[i] = n_agg;
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
+      if (strong[k]) agg[A.col[k]] = n_agg;
+    ++n_agg;
+  }
+  std::vector<int32_t> agg1 = agg;
+  for (int i = 0; i < A.nbr; ++i) {
+    if (agg[i] != -1) continue;
+    double best_s = 0.0;
+    int best_a = -1;
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      if (!strong[k]) continue;
+      int a = agg1[A.col[k]];
+      if (a < 0) continue;
+      if (best_a < 0 || s[k] > best_s || (s[k] == best_s && a < best_a)) {
+        best_s = s[k];
+        best_a = a;
+      }
+    }
+    if (best_a < 0) fail("aggregation left a node without an aggregated neighbour");
+    agg[i] = best_a;
+  }
+  *n_agg_out = n_agg;
+  return agg;
+}
+
+std::vector<double> spai0(const HBsr& A) {
+  const int B = A.br, bs = B * B;
+  auto dp = diag_pos(A);
+  std::vector<double> M((size_t)A.nbr * bs);
+  std::vector<double> G(bs), Gi(bs);
+  for (int i = 0; i < A.nbr; ++i) {
+    std::fill(G.begin(), G.end(), 0.0);
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      const double* a = &A.val[(size_t)k * bs];
+      for (int r = 0; r < B; ++r)
+        for (int c = 0; c < B; ++c) {
+          double acc = 0.0;
+          for (int t = 0; t < B; ++t) acc += a[r * B + t] * a[c * B + t];
+          G[r * B + c] += acc;
+        }
+    }
+    if (!blk_inv(B, G.data(), Gi.data()))
+      fail("SPAI0 Gram matrix is singular at row " + std::to_string(i) + " (zero row?)");
+    const double* d = &A.val[(size_t)dp[i] * bs];
+    double* m = &M[(size_t)i * bs];
+    for (int r = 0; r < B; ++r)
+      for (int c = 0; c < B; ++c) {
+        double acc = 0.0;
+        for (int t = 0; t < B; ++t) acc += d[t * B + r] * Gi[t * B + c];
+        m[r * B + c] = acc;
+      }
+  }
+  return M;
+}
+
+std::vector<double> jacobi(const HBsr& A, double omega) {
+  auto M = block_diag_inv(A);
+  for (auto& v : M) v *= omega;
+  return M;
+}
+
+HAmg build_amg(const HBsr& A0, const AmgSetupParams& prm) {
+  validate(A0, true);
+  HAmg H;
+  H.B = A0.br;
+  const int B = H.B, bs = B * B;
+  HBsr A = A0;
+  int l = 0;
+  while ((int64_t)A.nbr * B > prm.coarse_enough && l < prm.max_levels - 1) {
+    int n_agg = 0;
+    auto agg = aggregate(A, std::ldexp(prm.eps_strong, -l), &n_agg);
+    if (n_agg >= A.nbr) break;
+    HLevel lev;
+    lev.agg = agg;
+    // smoothed prolongator, row by row
+    HBsr P;
+    P.nbr = A.nbr;
+    P.nbc = n_agg;
+    P.br = P.bc = B;
+    P.ptr.assign(A.nbr + 1, 0);
+    double omega = 0.0;
+    std::vector<double> DinvA;
+    if (prm.smooth_P) {
+      auto Dinv = block_diag_inv(A);
+      HBsr DA = A;
+      for (int i = 0; i < A.nbr; ++i)
+        for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+          std::fill(&DA.val[(size_t)k * bs], &DA.val[(size_t)(k + 1) * bs], 0.0);
+          blk_mul_add(B, &Dinv[(size_t)i * bs], &A.val[(size_t)k * bs], &DA.val[(size_t)k * bs]);
+        }
+      double rho = spectral_radius(DA, prm.power_iters);
+      if (!(rho > 0.0)) fail("spectral radius estimate is zero");
+      omega = (4.0 / 3.0) / rho;
+      std::vector<int> mark(n_agg, -1);
+      std::vector<int> cols;
+      std::vector<double> acc;
+      for (int i = 0; i < A.nbr; ++i) {
+        cols.clear();
+        acc.clear();
+        for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+          int a = agg[A.col[k]];
+          if (mark[a] < 0) {
+            mark[a] = (int)cols.size();
+            cols.push_back(a);
+            acc.resize(acc.size() + bs, 0.0);
+          }
+          double* t = &acc[(size_t)mark[a] * bs];
+          const double* v = &DA.val[(size_t)k * bs];
+          for (int e = 0; e < bs; ++e) t[e] += v[e];
+        }
+        std::vector<int> order(cols.size());
+        for (size_t t = 0; t < order.size(); ++t) order[t] = (int)t;
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return cols[a] < cols[b]; });
+        for (int t : order) {
+          int a = cols[t];
+          P.col.push_back(a);
+          for (int r = 0; r < B; ++r)
+            for (int c = 0; c < B; ++c) {
+              double id = (a == agg[i] && r == c) ? 1.0 : 0.0;
+              P.val.push_back(id - omega * acc[(size_t)t * bs + r * B + c]);
+            }
+        }
+        for (int a : cols) mark[a] = -1;
+        P.ptr[i + 1] = (int32_t)P.col.size();
+      }
+    } else {
+      for (int i = 0; i < A.nbr; ++i) {
+        P.col.push_back(agg[i]);
+        for (int r = 0; r < B; ++r)
+          for (int c = 0; c < B; ++c) P.val.push_back(r == c ? 1.0 : 0.0);
+        P.ptr[i + 1] = i + 1;
+      }
+    }
+    lev.omega = omega;
+    HBsr R = transpose(P);
+    HBsr AP = spgemm(A, P);
+    HBsr Ac = spgemm(R, AP);
+    lev.M = prm.relax == 0 ? spai0(A) : jacobi(A, prm.jacobi_omega);
+    lev.A = std::move(A);
+    lev.P = std::move(P);
+    lev.R = std::move(R);
+    H.levels.push_back(std::move(lev));
+    A = std::move(Ac);
+    ++l;
+  }
+  if ((int64_t)A.nbr * B > 8192)
+    fail("coarsest level has " + std::to_string((int64_t)A.nbr * B) +
+         " unknowns (> 8192); raise max_levels or coarse_enough");
+  H.Ainv = dense_inverse(A);
+  H.Ac = std::move(A);
+  return H;
+}
+
+HSchur schur_split(const HBsr& K, int nvel) {
+  validate(K, true);
+  const int B = nvel + 1;
+  if (K.br != B) fail("Schur split needs bdim = nvel + 1");
+  HSchur S;
+  S.nvel = nvel;
+  auto mk = [&](int br, int bc) {
+    HBsr M;
+    M.nbr = K.nbr;
+    M.nbc = K.nbc;
+    M.br = br;
+    M.bc = bc;
+    M.ptr = K.ptr;
+    M.col = K.col;
+    M.val.resize((size_t)K.nnzb() * br * bc);
+    return M;
+  };
+  S.A = mk(nvel, nvel);
+  S.G = mk(nvel, 1);
+  S.D = mk(1, nvel);
+  S.C = mk(1, 1);
+  const int bs = B * B;
+  for (int64_t k = 0; k < K.nnzb(); ++k) {
+    const double* v = &K.val[(size_t)k * bs];
+    for (int r = 0; r < nvel; ++r) {
+      for (int c = 0; c < nvel; ++c) S.A.val[(size_t)k * nvel * nvel + r * nvel + c] = v[r * B + c];
+      S.G.val[(size_t)k * nvel + r] = v[r * B + nvel];
+      S.D.val[(size_t)k * nvel + r] = v[nvel * B + r];
+    }
+    S.C.val[k] = v[nvel * B + nvel];
+  }
+  // S_hat = C - diag(D diag(A)^-1 G)   (Eq. SchurApprox)
+  auto dp = diag_pos(S.A);
+  std::vector<double> dA((size_t)K.nbr * nvel);
+  for (int i = 0; i < K.nbr; ++i)
+    for (int c = 0; c < nvel; ++c) {
+      dA[(size_t)i * nvel + c] = S.A.val[(size_t)dp[i] * nvel * nvel + c * nvel + c];
+      if (dA[(size_t)i * nvel + c] == 0.0) fail("zero on the velocity diagonal");
+    }
+  S.S = S.C;
+  auto dpc = diag_pos(S.C);
+  for (int i = 0; i < K.nbr; ++i) {
+    double corr = 0.0;
+    for (int k = K.ptr[i]; k < K.ptr[i + 1]; ++k) {
+      int j = K.col[k];
+      int kt = find_col(K, j, i);
+      if (kt < 0) continue;
+      for (int c = 0; c < nvel; ++c)
+        corr += S.D.val[(size_t)k * nvel + c] * (1.0 / dA[(size_t)j * nvel + c]) *
+                S.G.val[(size_t)kt * nvel + c];
+    }
+    S.S.val[dpc[i]] -= corr;
+  }
+  return S;
+}
+
+bool transpose_map(const HBsr& A, std::vector<int32_t>& tmap) {
+  tmap.assign(A.nnzb(), -1);
+  for (int i = 0; i < A.nbr; ++i)
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      int j = A.col[k];
+      if (j >= A.nbr) return false;
+      int t = find_col(A, j, i);
+      if (t < 0) return false;
+      tmap[k] = t;
+    }
+  return true;
+}
+
+}  // namespace gbs

@@ -1,0 +1,76 @@
+// Host-side hierarchy construction (not on the solve path).
+//
+// The paper's AMGCL builds the multigrid hierarchy on builtin host
+// structures and then moves it to the backend (Section 2).  This file
+// declares that host step: smoothed-aggregation coarsening, SPAI0 /
+// damped-Jacobi blocks, the dense coarse inverse and the Schur split
+// (Eq. SchurPC / Eq. SchurApprox).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace gbs {
+
+// Block-CSR on the host, FP64 values, (br x bc) blocks, row-major blocks.
+struct HBsr {
+  int nbr = 0, nbc = 0, br = 1, bc = 1;
+  std::vector<int32_t> ptr, col;
+  std::vector<double> val;
+  int64_t nnzb() const { return (int64_t)col.size(); }
+  int bsz() const { return br * bc; }
+};
+
+struct AmgSetupParams {
+  double eps_strong = 0.08;
+  int coarse_enough = 1000;
+  int max_levels = 10;
+  int relax = 0;           // 0 SPAI0, 1 damped Jacobi
+  double jacobi_omega = 0.72;
+  bool smooth_P = true;
+  int power_iters = 20;
+};
+
+struct HLevel {
+  HBsr A, P, R;
+  std::vector<double> M;   // n_brows * B * B smoother blocks
+  std::vector<int32_t> agg;
+  double omega = 0.0;
+};
+
+struct HAmg {
+  int B = 1;
+  std::vector<HLevel> levels;   // all but the coarsest
+  HBsr Ac;                      // coarsest operator
+  std::vector<double> Ainv;     // dense inverse of Ac, row-major
+};
+
+struct SetupError {
+  std::string msg;
+};
+
+// Structural validation of a caller matrix (throws SetupError).
+void validate(const HBsr& A, bool square);
+
+// Full setup of one AMG hierarchy (throws SetupError).
+HAmg build_amg(const HBsr& A, const AmgSetupParams& prm);
+
+// Pieces exposed for tests / export.
+std::vector<int32_t> aggregate(const HBsr& A, double eps, int* n_agg);
+std::vector<double> spai0(const HBsr& A);
+std::vector<double> jacobi(const HBsr& A, double omega);
+
+// Schur split of node blocks (nvel+1)^2 into A (nvel^2), G (nvel x 1),
+// D (1 x nvel), C (1x1) on K's block pattern, and S_hat of Eq. SchurApprox.
+struct HSchur {
+  HBsr A, G, D, C, S;
+  int nvel = 3;
+};
+HSchur schur_split(const HBsr& K, int nvel);
+
+// Transpose map of a structurally symmetric pattern: tmap[k] = index of
+// block (j, i) for block k = (i, j).  Returns false if not symmetric.
+bool transpose_map(const HBsr& A, std::vector<int32_t>& tmap);
+
+}  // namespace gbs

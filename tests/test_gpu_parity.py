@@ -1,0 +1,359 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (FP64 forms): SpMV elementwise |y - y_ref| <= 1e-13 (|A||x|)_i
+(the rounding bound of a dot product of <= 48 terms is ~48 eps); V-cycle
+and Schur applications on the same (imported) hierarchy 1e-12 relative in
+the max norm; whole solves reach the 1e-8 true relative residual with an
+iteration count within +-10% of the oracle's.  Mixed forms (FP32/BF16
+hierarchies) are judged by the FP64 true residual and report their error
+against the oracle solution.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import stokes_inputs as si
+from oracle import adjoint, amg, bsr, krylov, schur
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2006_06052_gb300 as gb  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gb.build()
+    return gb.load_library()
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def rel_inf(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def check_spmv(H, A, x, transpose=False):
+    y = host(gb.spmv(H, dev(x), transpose=transpose))
+    Asp = A.scipy().T if transpose else A.scipy()
+    ref = Asp @ x
+    bound = abs(Asp) @ np.abs(x)
+    assert np.all(np.abs(y - ref) <= 1e-13 * bound + 1e-300)
+
+
+# ------------------------------------------------------------------ SpMV
+@pytest.mark.parametrize("case", ["c1_csr", "c2_bsr4", "vel_bsr3"])
+def test_outer_spmv_and_transpose(case):
+    N = 9   # 729 nodes: a ragged tail for every rows-per-warp grouping
+    if case == "c1_csr":
+        s = si.make_system("c1", N=N)
+        A = bsr.from_arrays(s.indptr, s.indices, s.data, 1)
+        ip, ix, d, B = s.indptr, s.indices, s.data, 1
+    elif case == "c2_bsr4":
+        s = si.make_system("c2", N=N)
+        A = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+        ip, ix, d, B = s.indptr, s.indices, s.data, 4
+    else:
+        s = si.make_system("c3", N=N)
+        A = schur.split(bsr.from_arrays(s.indptr, s.indices, s.data, 4)).A
+        ip, ix, d, B = A.indptr, A.indices, A.data, 3
+    H = gb.build_hierarchy(ip, ix, d, B, gb.params_default(relax=gb.GBS_JACOBI))
+    x = np.random.default_rng(1).standard_normal(A.shape[0])
+    check_spmv(H, A, x)
+    check_spmv(H, A, x, transpose=True)
+
+
+def test_paper_block_example_spmv():
+    """The 2x2-block matrix of the paper's Section 4 worked example."""
+    from conftest import load_golden
+    g = load_golden("paper_block_example.txt")
+    A = bsr.Bsr(np.array(g["bsr_ptr"], dtype=np.int64), np.array(g["bsr_col"], dtype=np.int64),
+                np.array(g["bsr_val"]).reshape(-1, 2, 2), 3)
+    H = gb.build_hierarchy(A.indptr, A.indices, A.data, 2, gb.params_default(enable_adjoint=0))
+    for seed in range(3):
+        x = np.random.default_rng(seed).standard_normal(6)
+        check_spmv(H, A, x)
+
+
+# ------------------------------------------------------- V-cycle / Schur
+def _import(Ho, B, **kw):
+    lv = Ho.levels
+    As = [(L.A.indptr, L.A.indices, L.A.data) for L in lv] + \
+         [(Ho.A_coarse.indptr, Ho.A_coarse.indices, Ho.A_coarse.data)]
+    Ps = [(L.P.indptr, L.P.indices, L.P.data, L.P.n_bcols) for L in lv]
+    Rs = [(L.R.indptr, L.R.indices, L.R.data, L.R.n_bcols) for L in lv]
+    Ms = [L.M for L in lv]
+    return gb.import_hierarchy(As, Ps, Rs, Ms, Ho.Ainv_coarse, B, gb.params_default(**kw))
+
+
+@pytest.mark.parametrize("cfg", [("c2", 9, "jacobi"), ("c2", 10, "spai0"), ("c1", 9, "spai0")])
+def test_vcycle_on_imported_oracle_hierarchy(cfg):
+    name, N, relax = cfg
+    s = si.make_system(name, N=N)
+    B = s.bdim
+    A = bsr.from_arrays(s.indptr, s.indices, s.data, B)
+    Ho = amg.build_hierarchy(A, amg.AmgParams(coarse_enough=50, relax=relax))
+    assert len(Ho.levels) >= 2
+    H = _import(Ho, B)
+    rng = np.random.default_rng(7)
+    for tr in (False, True):
+        r = rng.standard_normal(A.shape[0])
+        z = host(gb.apply_precond(H, dev(r), transpose=tr))
+        ref = amg.vcycle(Ho, r, 0, transpose=tr)
+        assert rel_inf(z, ref) <= 1e-12, (tr, rel_inf(z, ref))
+
+
+def test_vcycle_on_library_built_hierarchy():
+    s = si.make_system("c2", N=12)
+    A = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    Ho = amg.build_hierarchy(A, amg.AmgParams(coarse_enough=100, relax="jacobi"))
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
+                           gb.params_default(coarse_enough=100, relax=gb.GBS_JACOBI))
+    assert gb.hierarchy_info(H)["nlevels"] == Ho.nlevels
+    r = np.random.default_rng(3).standard_normal(A.shape[0])
+    z = host(gb.apply_precond(H, dev(r)))
+    assert rel_inf(z, amg.vcycle(Ho, r)) <= 1e-10
+
+
+def test_schur_apply_matches_oracle():
+    s = si.make_system("c3", N=9)
+    K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    po = amg.AmgParams(coarse_enough=60)
+    pc = schur.build(K, 3, po, po)
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
+                           gb.params_default(precond=gb.GBS_PC_SCHUR, krylov=gb.GBS_GMRES,
+                                             coarse_enough=60))
+    rng = np.random.default_rng(11)
+    for tr in (False, True):
+        r = rng.standard_normal(K.shape[0])
+        z = host(gb.apply_precond(H, dev(r), transpose=tr))
+        ref = pc.apply(r, transpose=tr)
+        assert rel_inf(z, ref) <= 1e-10, (tr, rel_inf(z, ref))
+
+
+@pytest.mark.parametrize("precision", [gb.GBS_FP32, gb.GBS_BF16])
+def test_mixed_vcycle_close_to_fp64(precision):
+    """Mixed forms: the cast hierarchy's V-cycle stays within the storage
+    precision of the FP64 one (FP32 ~1e-6, BF16 ~1e-2 relative)."""
+    s = si.make_system("c2", N=10)
+    p64 = gb.params_default(relax=gb.GBS_JACOBI, coarse_enough=60)
+    pmx = gb.params_default(relax=gb.GBS_JACOBI, coarse_enough=60, precision=precision)
+    H64 = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, p64)
+    Hmx = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, pmx)
+    r = dev(np.random.default_rng(2).standard_normal(s.n))
+    z64 = host(gb.apply_precond(H64, r))
+    zmx = host(gb.apply_precond(Hmx, r))
+    tol = 1e-4 if precision == gb.GBS_FP32 else 1e-1
+    assert rel_inf(zmx, z64) <= tol
+
+
+# ----------------------------------------------------------------- solves
+def _oracle_solve(s, relax, coarse_enough=1000):
+    K = bsr.from_arrays(s.indptr, s.indices, s.data, s.bdim)
+    Ks = K.scipy()
+    if s.method == "amg_bicgstab":
+        Ho = amg.build_hierarchy(K, amg.AmgParams(relax=relax, coarse_enough=coarse_enough))
+        return krylov.bicgstab(lambda v: Ks @ v, lambda v: amg.vcycle(Ho, v), s.b, tol=1e-8)
+    pc = schur.build(K, 3, amg.AmgParams(coarse_enough=coarse_enough),
+                     amg.AmgParams(coarse_enough=coarse_enough))
+    return krylov.gmres(lambda v: Ks @ v, pc.apply, s.b, m=30, tol=1e-8)
+
+
+def _true_rel(s, x):
+    return np.linalg.norm(s.b - s.scipy() @ x) / np.linalg.norm(s.b)
+
+
+def _params(s, **kw):
+    if s.method == "amg_bicgstab":
+        return gb.params_default(**kw)
+    return gb.params_default(precond=gb.GBS_PC_SCHUR, krylov=gb.GBS_GMRES, **kw)
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_solve_c1_full_size(use_graph):
+    """C1: N=16 scalar CSR, SA-AMG (SPAI0 1+1) + BiCGStab to 1e-8."""
+    s = si.make_system("c1")
+    xo, io = _oracle_solve(s, "spai0")
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 1, _params(s, use_graph=use_graph))
+    x, info = gb.solve(H, dev(s.b))
+    x = host(x)
+    assert info.converged and _true_rel(s, x) <= 1e-8
+    assert abs(info.iters - io.iters) <= max(1, math.ceil(0.1 * io.iters)), (info.iters, io.iters)
+    assert np.linalg.norm(x - s.x_exact) / np.linalg.norm(s.x_exact) < 1e-5
+
+
+@pytest.mark.parametrize("N", [13, 16])
+def test_solve_c2_recipe(N):
+    s = si.make_system("c2", N=N)
+    xo, io = _oracle_solve(s, "jacobi")
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, _params(s, relax=gb.GBS_JACOBI))
+    x, info = gb.solve(H, dev(s.b))
+    x = host(x)
+    assert info.converged and _true_rel(s, x) <= 1e-8
+    assert abs(info.iters - io.iters) <= max(1, math.ceil(0.1 * io.iters)), (info.iters, io.iters)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-5
+
+
+@pytest.mark.parametrize("precision", [gb.GBS_FP64, gb.GBS_FP32, gb.GBS_BF16])
+def test_solve_c3_recipe_forms(precision):
+    s = si.make_system("c3", N=14)
+    xo, io = _oracle_solve(s, "spai0")
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, _params(s, precision=precision))
+    x, info = gb.solve(H, dev(s.b))
+    x = host(x)
+    assert info.converged and _true_rel(s, x) <= 1e-8
+    err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+    assert err < 1e-5
+    if precision == gb.GBS_FP64:
+        assert abs(info.iters - io.iters) <= max(1, math.ceil(0.1 * io.iters))
+
+
+def test_solve_edge_cases():
+    s = si.make_system("c2", N=6)
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, _params(s, relax=gb.GBS_JACOBI))
+    # zero right-hand side: x = 0, no iterations
+    x, info = gb.solve(H, dev(np.zeros(s.n)), dev(np.ones(s.n)))
+    assert info.converged and info.iters == 0 and not host(x).any()
+    # a converged start returns immediately (warm start)
+    x1, info1 = gb.solve(H, dev(s.b))
+    x2, info2 = gb.solve(H, dev(s.b), x1.clone())
+    assert info2.iters == 0 and info2.converged
+    # maxiter = 1: not converged, x and info still written
+    H1 = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
+                            _params(s, relax=gb.GBS_JACOBI, maxiter=1, tol=1e-14))
+    x, info = gb.solve(H1, dev(s.b))
+    assert not info.converged and info.iters == 1 and info.status == 1
+    assert info.rel_res < 1.0
+    # NaN in b is reported, not propagated silently
+    b = s.b.copy()
+    b[3] = np.nan
+    with pytest.raises(gb.GbsError) as e:
+        gb.solve(H, dev(b))
+    assert e.value.status == -5
+
+
+def test_gmres_edge_cases():
+    s = si.make_system("c3", N=5)
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, _params(s, coarse_enough=40))
+    x, info = gb.solve(H, dev(np.zeros(s.n)))
+    assert info.converged and info.iters == 0
+    H2 = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
+                            _params(s, coarse_enough=40, restart=4, maxiter=3, tol=1e-14))
+    x, info = gb.solve(H2, dev(s.b))
+    assert not info.converged and info.iters == 3
+
+
+# ---------------------------------------------------------------- adjoint
+def test_sampled_outer_matches_oracle():
+    s = si.make_system("c2", N=7)
+    K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, _params(s, relax=gb.GBS_JACOBI))
+    rng = np.random.default_rng(5)
+    lam, x = rng.standard_normal((2, s.n))
+    g = host(gb.sampled_outer(H, dev(lam), dev(x), -1.0)).reshape(-1, 4, 4)
+    ref = adjoint.sampled_outer(K, lam, x, -1.0)
+    assert np.array_equal(g, ref)
+
+
+@pytest.mark.parametrize("method", ["amg_bicgstab", "schur_gmres"])
+def test_adjoint_matches_dense_inverse(method):
+    name = "c2" if method == "amg_bicgstab" else "c3"
+    s = si.make_system(name, N=5)
+    Kd = s.scipy().toarray()
+    xt = si.gaussian_vector(s.n, 4001)
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
+                           _params(s, relax=gb.GBS_JACOBI, coarse_enough=40, tol=1e-12))
+    x, _ = gb.solve(H, dev(s.b))
+    lam, info = gb.solve_adjoint(H, x - dev(xt))
+    assert info.converged
+    xd = np.linalg.solve(Kd, s.b)
+    lamd = np.linalg.solve(Kd.T, xd - xt)
+    np.testing.assert_allclose(host(lam), lamd, rtol=0, atol=1e-8 * np.abs(lamd).max())
+
+
+def test_autograd_gradients_match_dense_inverse():
+    from paper_2006_06052_gb300.autograd import stokes_solve
+    s = si.make_system("c2", N=5)
+    K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    Kd = K.dense()
+    xt = si.gaussian_vector(s.n, 4001)
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
+                           _params(s, relax=gb.GBS_JACOBI, coarse_enough=40, tol=1e-12))
+    vals = dev(s.data.reshape(-1)).requires_grad_(True)
+    b = dev(s.b).requires_grad_(True)
+    x = stokes_solve(vals, b, H)
+    loss = 0.5 * ((x - dev(xt)) ** 2).sum()
+    loss.backward()
+    xd = np.linalg.solve(Kd, s.b)
+    lamd = np.linalg.solve(Kd.T, xd - xt)
+    np.testing.assert_allclose(host(b.grad), lamd, rtol=0, atol=1e-8 * np.abs(lamd).max())
+    gref = adjoint.sampled_outer(K, lamd, xd, -1.0).reshape(-1)
+    np.testing.assert_allclose(host(vals.grad), gref, rtol=0, atol=1e-8 * np.abs(gref).max())
+
+
+def test_autograd_central_differences_c4_recipe():
+    """C4 recipe at N=6: FP64 central differences (h = 1e-6) of
+    L = 1/2 ||x - x_t||^2 on sampled entries, solves to 1e-13 through
+    gbs_update_values (hierarchy reused), vs the adjoint gradient."""
+    from paper_2006_06052_gb300.autograd import stokes_solve
+    s = si.make_system("c4", N=6)
+    xt = dev(si.gaussian_vector(s.n, 4001))
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
+                           _params(s, relax=gb.GBS_JACOBI, coarse_enough=100, tol=1e-13))
+    v0 = dev(s.data.reshape(-1))
+    vals = v0.clone().requires_grad_(True)
+    x = stokes_solve(vals, dev(s.b), H)
+    (0.5 * ((x - xt) ** 2).sum()).backward()
+    G = host(vals.grad)
+    rng = np.random.Generator(np.random.PCG64(4002))
+    nz = np.nonzero(s.data.reshape(-1))[0]
+    for idx in rng.choice(nz, size=8, replace=False):
+        step = 1e-6 * max(1.0, abs(float(s.data.reshape(-1)[idx])))
+        vp = v0.clone()
+        vm = v0.clone()
+        vp[idx] += step
+        vm[idx] -= step
+        with torch.no_grad():
+            xp = stokes_solve(vp, dev(s.b), H)
+            xm = stokes_solve(vm, dev(s.b), H)
+        dl = 0.5 * torch.dot(xp - xm, xp + xm - 2 * xt).item()
+        fd = dl / (2 * step)
+        assert abs(fd - G[idx]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(G).max()), (idx, fd, G[idx])
+
+
+# ------------------------------------------------------------ full sizes
+def test_full_size_c2_against_oracle():
+    """C2 at full size (N=64, 1,048,576 unknowns, 4x4 BSR FP64), the
+    benchmarked configuration: true residual (oracle SpMV) <= 1e-8 and
+    iteration count within +-10% of the oracle's solve."""
+    s = si.make_system("c2")
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, _params(s, relax=gb.GBS_JACOBI))
+    x, info = gb.solve(H, dev(s.b))
+    x = host(x)
+    assert info.converged and _true_rel(s, x) <= 1e-8
+    xo, io = _oracle_solve(s, "jacobi")
+    assert abs(info.iters - io.iters) <= max(1, math.ceil(0.1 * io.iters)), (info.iters, io.iters)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-5
+
+
+@pytest.mark.parametrize("precision", [gb.GBS_FP64, gb.GBS_BF16])
+def test_full_size_c3_true_residual(precision):
+    """C3 at full size (N=128, 8,388,608 unknowns): the FP64 true residual,
+    recomputed on the host with the oracle's SpMV, is <= 1e-8."""
+    s = si.make_system("c3")
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, _params(s, precision=precision,
+                                                                    enable_adjoint=0))
+    x, info = gb.solve(H, dev(s.b))
+    x = host(x)
+    assert info.converged
+    assert _true_rel(s, x) <= 1e-8
