@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "device.hpp"
 #include "kernels.cuh"
@@ -59,7 +60,7 @@ std::vector<VT> cast_vec(const std::vector<double>& v) {
   return o;
 }
 
-template <class VT>
+template <class VT, class AT>
 DevBsr<VT> upload_bsr(Arena& ar, const HBsr& H, bool with_tmap, cudaStream_t s,
                       std::vector<std::vector<VT>>& keep) {
   DevBsr<VT> d;
@@ -69,6 +70,16 @@ DevBsr<VT> upload_bsr(Arena& ar, const HBsr& H, bool with_tmap, cudaStream_t s,
   d.col = ar.upload(H.col.data(), H.col.size(), s);
   keep.push_back(cast_vec<VT>(H.val));
   d.val = ar.upload(keep.back().data(), keep.back().size(), s);
+  switch (H.br) {
+    case 1: d.G = choose_group<1, VT, AT>(H.nbr, H.nnzb()); break;
+    case 2: d.G = choose_group<2, VT, AT>(H.nbr, H.nnzb()); break;
+    case 3: d.G = choose_group<3, VT, AT>(H.nbr, H.nnzb()); break;
+    default: d.G = choose_group<4, VT, AT>(H.nbr, H.nnzb()); break;
+  }
+  if (const char* e = std::getenv("GBS_SPMV_GROUP")) {  // tuning override: 0, 8, 16, 32, 256
+    int g = std::atoi(e);
+    if (g == 0 || g == 8 || g == 16 || g == 32 || g == 256) d.G = g;
+  }
   if (with_tmap) {
     std::vector<int32_t> tm;
     if (!transpose_map(H, tm))
@@ -82,7 +93,15 @@ DevBsr<VT> upload_bsr(Arena& ar, const HBsr& H, bool with_tmap, cudaStream_t s,
 template <int B, bool TR, int MODE, class VT, class XT, class YT, class AT>
 void spmv_B(const DevBsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
   if (A.nbr == 0) return;
-  k_spmv<B, TR, MODE, VT, XT, YT, AT><<<grid_for(row_threads<B>(A.nbr)), 256, 0, s>>>(A, x, f, y);
+  const int64_t nt = (int64_t)A.nbr * A.G;
+  switch (A.G) {
+    case 8: k_spmv_w<B, 8, TR, MODE, VT, XT, YT, AT><<<grid_for(nt), 256, 0, s>>>(A, x, f, y); break;
+    case 16: k_spmv_w<B, 16, TR, MODE, VT, XT, YT, AT><<<grid_for(nt), 256, 0, s>>>(A, x, f, y); break;
+    case 32: k_spmv_w<B, 32, TR, MODE, VT, XT, YT, AT><<<grid_for(nt), 256, 0, s>>>(A, x, f, y); break;
+    case 256: k_spmv_w<B, 256, TR, MODE, VT, XT, YT, AT><<<grid_for(nt), 256, 0, s>>>(A, x, f, y); break;
+    default:
+      k_spmv<B, TR, MODE, VT, XT, YT, AT><<<grid_for(row_threads<B>(A.nbr)), 256, 0, s>>>(A, x, f, y);
+  }
 }
 template <bool TR, int MODE, class VT, class XT, class YT, class AT>
 void spmv(int B, const DevBsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
@@ -98,8 +117,14 @@ template <bool TR, class VT, class XT, class AT>
 void relax(int B, const DevBsr<VT>& A, const VT* M, const XT* f, const XT* x, XT* xo,
            cudaStream_t s) {
   if (A.nbr == 0) return;
-#define GBS_RELAX(BB) \
-  k_relax<BB, TR, VT, XT, AT><<<grid_for(row_threads<BB>(A.nbr)), 256, 0, s>>>(A, M, f, x, xo)
+#define GBS_RELAX(BB)                                                                            \
+  switch (A.G) {                                                                                 \
+    case 8: k_relax_w<BB, 8, TR, VT, XT, AT><<<grid_for((int64_t)A.nbr * 8), 256, 0, s>>>(A, M, f, x, xo); break;   \
+    case 16: k_relax_w<BB, 16, TR, VT, XT, AT><<<grid_for((int64_t)A.nbr * 16), 256, 0, s>>>(A, M, f, x, xo); break; \
+    case 32: k_relax_w<BB, 32, TR, VT, XT, AT><<<grid_for((int64_t)A.nbr * 32), 256, 0, s>>>(A, M, f, x, xo); break; \
+    case 256: k_relax_w<BB, 256, TR, VT, XT, AT><<<grid_for((int64_t)A.nbr * 256), 256, 0, s>>>(A, M, f, x, xo); break; \
+    default: k_relax<BB, TR, VT, XT, AT><<<grid_for(row_threads<BB>(A.nbr)), 256, 0, s>>>(A, M, f, x, xo);         \
+  }
   switch (B) {
     case 1: GBS_RELAX(1); break;
     case 2: GBS_RELAX(2); break;
@@ -163,9 +188,9 @@ struct DevAmg {
       const HLevel& h = H.levels[l];
       Lev L;
       L.n = (int64_t)h.A.nbr * B;
-      L.A = upload_bsr<VT>(ar, h.A, o.tmaps, s, keep);
-      L.Pm = upload_bsr<VT>(ar, h.P, false, s, keep);
-      L.R = upload_bsr<VT>(ar, h.R, false, s, keep);
+      L.A = upload_bsr<VT, AT>(ar, h.A, o.tmaps, s, keep);
+      L.Pm = upload_bsr<VT, AT>(ar, h.P, false, s, keep);
+      L.R = upload_bsr<VT, AT>(ar, h.R, false, s, keep);
       keep.push_back(cast_vec<VT>(h.M));
       L.M = ar.upload(keep.back().data(), keep.back().size(), s);
       L.f = ar.alloc<ST>(L.n);
@@ -358,6 +383,7 @@ template <int P>
 struct SchurPrecond final : DevPrecond {
   using VT = typename FormT<P>::VT;
   using ST = typename FormT<P>::ST;
+  using AT = ST;
   DevAmg<P> A, S;
   DevBsr<VT> G, D;  // share K's pattern; val = coupling values
   int nv = 3, nn = 0;
@@ -373,7 +399,7 @@ struct SchurPrecond final : DevPrecond {
     A.build(HA, o, s);
     S.build(HS, o, s);
     std::vector<std::vector<VT>> keep;
-    G = upload_bsr<VT>(ar, Hs.G, o.tmaps, s, keep);
+    G = upload_bsr<VT, AT>(ar, Hs.G, o.tmaps, s, keep);
     D.nbr = Hs.D.nbr;
     D.nbc = Hs.D.nbc;
     D.rp = G.rp;

@@ -10,6 +10,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -136,6 +137,16 @@ void alloc_work(Handle& h, cudaStream_t s) {
   h.K.rp = a.upload(h.Kh.ptr.data(), h.Kh.ptr.size(), s);
   h.K.col = a.upload(h.Kh.col.data(), h.Kh.col.size(), s);
   h.K.val = h.Kval;
+  switch (h.B) {
+    case 1: h.K.G = choose_group<1, double, double>(h.Kh.nbr, h.Kh.nnzb()); break;
+    case 2: h.K.G = choose_group<2, double, double>(h.Kh.nbr, h.Kh.nnzb()); break;
+    case 3: h.K.G = choose_group<3, double, double>(h.Kh.nbr, h.Kh.nnzb()); break;
+    default: h.K.G = choose_group<4, double, double>(h.Kh.nbr, h.Kh.nnzb()); break;
+  }
+  if (const char* e = std::getenv("GBS_SPMV_GROUP")) {  // tuning override
+    int g = std::atoi(e);
+    if (g == 0 || g == 8 || g == 16 || g == 32) h.K.G = g;
+  }
   if (h.prm.enable_adjoint) {
     std::vector<int32_t> tm;
     if (!transpose_map(h.Kh, tm))
@@ -170,10 +181,21 @@ void alloc_work(Handle& h, cudaStream_t s) {
 // ----------------------------------------------------------- outer kernels
 template <bool TR, int MODE>
 void outer_B(const Handle& h, const double* x, const double* f, double* y, const double* w0,
-             const double* w1, int slot, int op, bool reduce, cudaStream_t s) {
+             int self_dot, int slot, int op, bool reduce, cudaStream_t s) {
   const Red& R = h.red;
-#define GBS_OUT(BB) \
-  k_outer<BB, TR, MODE><<<RED_BLOCKS, RED_THREADS, 0, s>>>(h.K, x, f, y, w0, w1, R, slot, op, reduce)
+#define GBS_OUTG(BB, GG) \
+  k_outer<BB, GG, TR, MODE><<<RED_BLOCKS, RED_THREADS, 0, s>>>(h.K, x, f, y, w0, self_dot, R, slot, \
+                                                                op, reduce)
+#define GBS_OUT(BB)                                                                        \
+  switch (h.K.G) {                                                                         \
+    case 0:                                                                                \
+      k_outer_n<BB, TR, MODE><<<RED_BLOCKS, RED_THREADS, 0, s>>>(h.K, x, f, y, w0, self_dot, R, \
+                                                                  slot, op, reduce);       \
+      break;                                                                               \
+    case 8: GBS_OUTG(BB, 8); break;                                                        \
+    case 16: GBS_OUTG(BB, 16); break;                                                      \
+    default: GBS_OUTG(BB, 32); break;                                                      \
+  }
   switch (h.B) {
     case 1: GBS_OUT(1); break;
     case 2: GBS_OUT(2); break;
@@ -181,16 +203,18 @@ void outer_B(const Handle& h, const double* x, const double* f, double* y, const
     case 4: GBS_OUT(4); break;
   }
 #undef GBS_OUT
+#undef GBS_OUTG
   GBS_LAUNCH_CHECK();
 }
+// y = K x or f - K x (K^T when tr); d0 = y . w0 (w0 != y), d1 = y . y if self_dot.
 void outer(const Handle& h, bool tr, int mode, const double* x, const double* f, double* y,
-           const double* w0, const double* w1, int slot, int op, bool reduce, cudaStream_t s) {
+           const double* w0, int self_dot, int slot, int op, bool reduce, cudaStream_t s) {
   if (tr) {
-    if (mode == SPMV_RESID) outer_B<true, SPMV_RESID>(h, x, f, y, w0, w1, slot, op, reduce, s);
-    else outer_B<true, SPMV_SET>(h, x, f, y, w0, w1, slot, op, reduce, s);
+    if (mode == SPMV_RESID) outer_B<true, SPMV_RESID>(h, x, f, y, w0, self_dot, slot, op, reduce, s);
+    else outer_B<true, SPMV_SET>(h, x, f, y, w0, self_dot, slot, op, reduce, s);
   } else {
-    if (mode == SPMV_RESID) outer_B<false, SPMV_RESID>(h, x, f, y, w0, w1, slot, op, reduce, s);
-    else outer_B<false, SPMV_SET>(h, x, f, y, w0, w1, slot, op, reduce, s);
+    if (mode == SPMV_RESID) outer_B<false, SPMV_RESID>(h, x, f, y, w0, self_dot, slot, op, reduce, s);
+    else outer_B<false, SPMV_SET>(h, x, f, y, w0, self_dot, slot, op, reduce, s);
   }
 }
 
@@ -206,11 +230,11 @@ void bicg_iteration(Handle& h, bool tr, cudaStream_t s) {
   k_bicg_p<<<g, 256, 0, s>>>(n, h.r, h.v, h.p, h.sc);
   GBS_LAUNCH_CHECK();
   h.pc->apply(h.p, h.ph, tr, s);
-  outer(h, tr, SPMV_SET, h.ph, nullptr, h.v, h.rhat, nullptr, 0, FIN_ALPHA, true, s);
+  outer(h, tr, SPMV_SET, h.ph, nullptr, h.v, h.rhat, 0, 0, FIN_ALPHA, true, s);
   k_bicg_s<<<g, 256, 0, s>>>(n, h.r, h.v, h.s, h.sc);
   GBS_LAUNCH_CHECK();
   h.pc->apply(h.s, h.sh, tr, s);
-  outer(h, tr, SPMV_SET, h.sh, nullptr, h.t, h.s, h.t, 1, FIN_OMEGA, true, s);
+  outer(h, tr, SPMV_SET, h.sh, nullptr, h.t, h.s, 1, 1, FIN_OMEGA, true, s);
   k_bicg_xr<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.xi, h.ph, h.sh, h.s, h.t, h.r, h.rhat, h.red, 2);
   GBS_LAUNCH_CHECK();
 }
@@ -281,7 +305,7 @@ gbs_status solve_bicgstab(Handle& h, const double* b, double* x, bool tr, cudaSt
   GBS_CUDA(cudaMemcpyAsync(h.xi, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
   GBS_LAUNCH_CHECK();
-  outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, h.r, 4, FIN_INIT, true, s);
+  outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, 1, 4, FIN_INIT, true, s);
   GBS_CUDA(cudaMemcpyAsync(h.rhat, h.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   read_scalars(h, s);
   const double bb = h.sc_host[S_BB];
@@ -315,7 +339,7 @@ gbs_status solve_bicgstab(Handle& h, const double* b, double* x, bool tr, cudaSt
     hist.push_back(res);
     const bool claim = res <= h.prm.tol;
     if (claim || it % h.prm.replace_every == 0) {
-      outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, h.rhat, h.r, 4, FIN_REPLACE, true, s);
+      outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, h.rhat, 1, 4, FIN_REPLACE, true, s);
       read_scalars(h, s);
       ++repl;
       rel = std::sqrt(h.sc_host[S_RR]) / nb;
@@ -338,7 +362,7 @@ gbs_status solve_bicgstab(Handle& h, const double* b, double* x, bool tr, cudaSt
     }
   }
   if (!conv) {
-    outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, h.r, 4, FIN_RR, true, s);
+    outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, 1, 4, FIN_RR, true, s);
     read_scalars(h, s);
     rel = std::sqrt(h.sc_host[S_RR]) / nb;
     conv = rel <= h.prm.tol;
@@ -390,7 +414,7 @@ gbs_status solve_gmres(Handle& h, const double* b, double* x, bool tr, cudaStrea
   double rel = INFINITY;
   bool conv = false;
   for (;;) {
-    outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, h.r, 4, FIN_RR, true, s);
+    outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, 1, 4, FIN_RR, true, s);
     read_scalars(h, s);
     ++repl;
     const double beta = std::sqrt(h.sc_host[S_RR]);
@@ -410,7 +434,7 @@ gbs_status solve_gmres(Handle& h, const double* b, double* x, bool tr, cudaStrea
     while (j < m && it < h.prm.maxiter) {
       double* w = h.V + (size_t)(j + 1) * n;
       h.pc->apply(h.V + (size_t)j * n, h.z, tr, s);
-      outer(h, tr, SPMV_SET, h.z, nullptr, w, nullptr, nullptr, 0, FIN_STORE, false, s);
+      outer(h, tr, SPMV_SET, h.z, nullptr, w, nullptr, 0, 0, FIN_STORE, false, s);
       const int J = j + 1;
       k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol, h.red, 5, nullptr);
       GBS_LAUNCH_CHECK();
@@ -716,8 +740,8 @@ gbs_status gbs_spmv(const gbs_hierarchy* hh, const double* x, double* y, int32_t
     need_aligned(x, "x");
     need_aligned(y, "y");
     if (transpose && !h.K.tmap) throw SetupError{"built without enable_adjoint"};
-    outer(h, transpose != 0, SPMV_SET, x, nullptr, y, nullptr, nullptr, 0, FIN_STORE, false,
-          S(stream));
+    if (x == y) throw SetupError{"x and y must not alias"};
+    outer(h, transpose != 0, SPMV_SET, x, nullptr, y, nullptr, 0, 0, FIN_STORE, false, S(stream));
     return GBS_OK;
   });
 }
@@ -730,6 +754,7 @@ gbs_status gbs_apply_precond(gbs_hierarchy* hh, const double* r, double* z, int3
     need_device(h);
     need_aligned(r, "r");
     need_aligned(z, "z");
+    if (r == z) throw SetupError{"r and z must not alias"};
     if (transpose && !h.prm.enable_adjoint) throw SetupError{"built without enable_adjoint"};
     h.pc->apply(r, z, transpose != 0, S(stream));
     return GBS_OK;

@@ -30,7 +30,9 @@ struct DevBsr {
   const int* col = nullptr;
   const VT* val = nullptr;
   const int* tmap = nullptr;  // transpose map (may be null)
+  int G = 0;                  // lanes per block row (0: one lane per scalar row)
 };
+
 
 // ---------------------------------------------------------------- conversions
 __device__ __forceinline__ float to_f(float v) { return v; }
@@ -139,6 +141,202 @@ __device__ __forceinline__ AT row_dot(const DevBsr<VT>& A, const XT* __restrict_
   return acc;
 }
 
+// Geometry of the coalesced "chunk streaming" read of one block row.  The
+// values of a block row are contiguous (nblk blocks of B*B values), so G
+// lanes read them as consecutive CB-byte chunks: a warp instruction covers
+// 32*CB contiguous bytes.  When a block is a power-of-two number LPB of
+// chunks and G is a multiple of LPB, lane g always sees the same position
+// p = g % LPB inside a block: a fixed run of E values belonging to row(s)
+// p*E/B, so it needs only E (or B) entries of x and one or two partial sums.
+// Otherwise (B = 3) lanes stream single values ("element" mode).
+template <int B, class VT>
+struct Geom {
+  static constexpr int BB = B * B * (int)sizeof(VT);
+  static constexpr int CB = BB % 16 == 0 ? 16 : (BB % 8 == 0 ? 8 : (BB % 4 == 0 ? 4 : (int)sizeof(VT)));
+  static constexpr int E = CB / (int)sizeof(VT);   // values per chunk
+  static constexpr int LPB = BB / CB;              // chunks per block
+  static constexpr bool FIXED = (LPB & (LPB - 1)) == 0 && LPB <= 8 && (E <= B ? B % E == 0 : E % B == 0);
+  static constexpr int NR = E > B ? E / B : 1;     // rows touched by one chunk
+  static constexpr int NX = E > B ? B : E;         // x entries one chunk needs
+};
+
+// Lanes per block row (0 = one lane per scalar row, no cross-lane sums).
+// FP64 accumulation is bound by GB300's FP64 pipe (about 2 DFMA per clock
+// per SM), where every cross-lane reduction adds log2(G)*B FP64 adds per
+// lane: FP64 keeps one lane per scalar row whenever that gives enough
+// threads, and uses lane groups only on short coarse levels.  FP32
+// accumulation is not ALU-bound and uses coalesced lane groups sized by
+// row length; a whole 256-thread CTA per row when there are few, very
+// long rows.
+template <int B, class VT, class AT>
+inline int choose_group(int64_t nbr, int64_t nnzb) {
+  using Gm = Geom<B, VT>;
+  const double avg = nbr ? (double)nnzb / nbr : 0.0;
+  const double chunks = avg * (Gm::FIXED ? Gm::LPB : B * B);
+  if (sizeof(AT) == 8) {
+    if (nbr * B >= 65536 || avg < 4.0) return 0;
+    if (chunks <= 96) return 8;
+    if (chunks <= 384 || nbr > 2048) return 16;
+    return 32;
+  }
+  if (chunks <= 48) return 8;
+  if (chunks <= 96) return 16;
+  if (chunks <= 768 || nbr > 4096) return 32;
+  return 256;
+}
+
+// Forward (A x)_brow with G lanes per block row (G in {8, 16, 32}, or 256 =
+// one CTA, in which case this returns per-warp partials: the caller
+// finishes the reduction across warps).  All 32 lanes of the warp must
+// call it; inactive groups pass ok = false.  On return every lane of the
+// group (warp) holds the complete B-vector.
+template <int B, int G, class VT, class XT, class AT>
+__device__ __forceinline__ void group_row_fwd(const DevBsr<VT>& A, const XT* __restrict__ x,
+                                              int brow, int g, bool ok, AT (&acc)[B]) {
+  using Gm = Geom<B, VT>;
+#pragma unroll
+  for (int r = 0; r < B; ++r) acc[r] = AT(0);
+  if (ok) {
+    const int k0 = A.rp[brow], k1 = A.rp[brow + 1];
+    const VT* __restrict__ vrow = A.val + (size_t)k0 * (B * B);
+    if constexpr (Gm::FIXED) {
+      const int p = g % Gm::LPB;
+      const int e0 = p * Gm::E;               // first value of the chunk in the block
+      const int r0 = e0 / B;
+      const int c0 = Gm::E <= B ? e0 % B : 0;
+      AT part[Gm::NR];
+#pragma unroll
+      for (int q = 0; q < Gm::NR; ++q) part[q] = AT(0);
+      const int nch = (k1 - k0) * Gm::LPB;
+      // U chunks per batch: all index and value loads of a batch are issued
+      // before the dependent x gathers, so each lane keeps 2U loads in flight.
+      constexpr int U = 4;
+      for (int cb = g; cb < nch; cb += U * G) {
+        // out-of-range slots re-read the row's last chunk (always valid:
+        // nch > 0 here) and are masked at the FMA, so no load is predicated
+        int cc[U], j[U];
+        AT v[U][Gm::E];
+#pragma unroll
+        for (int u = 0; u < U; ++u) cc[u] = min(cb + u * G, nch - 1);
+#pragma unroll
+        for (int u = 0; u < U; ++u) j[u] = __ldg(A.col + k0 + cc[u] / Gm::LPB);
+#pragma unroll
+        for (int u = 0; u < U; ++u) load_run<Gm::E, VT, AT, true>(vrow + (size_t)cc[u] * Gm::E, v[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          AT xv[Gm::NX];
+          load_run<Gm::NX, XT, AT, false>(x + (size_t)j[u] * B + c0, xv);
+          if (cb + u * G < nch) {
+#pragma unroll
+            for (int q = 0; q < Gm::NR; ++q)
+#pragma unroll
+              for (int e = 0; e < Gm::NX; ++e) part[q] += v[u][q * Gm::NX + e] * xv[e];
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < B; ++r)
+#pragma unroll
+        for (int q = 0; q < Gm::NR; ++q)
+          if (r == r0 + q) acc[r] += part[q];
+    } else {
+      const int ne = (k1 - k0) * (B * B);
+      constexpr int U = 4;
+      for (int eb = g; eb < ne; eb += U * G) {
+        int j[U], rr[U], cl[U], ee[U];
+        AT v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          ee[u] = min(eb + u * G, ne - 1);
+          const int kb = ee[u] / (B * B);
+          const int w = ee[u] - kb * (B * B);
+          rr[u] = w / B;
+          cl[u] = w - rr[u] * B;
+          j[u] = __ldg(A.col + k0 + kb);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = cvt<AT>(__ldcs(vrow + ee[u]));
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const AT xv = cvt<AT>(__ldg(x + (size_t)j[u] * B + cl[u]));
+          if (eb + u * G < ne) {
+#pragma unroll
+            for (int q = 0; q < B; ++q)
+              if (q == rr[u]) acc[q] += v[u] * xv;
+          }
+        }
+      }
+    }
+  }
+  constexpr int W = G < 32 ? G : 32;
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int r = 0; r < B; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+}
+
+// Transposed (A^T x)_brow through the transpose map: lane g takes whole
+// blocks k0+g, k0+g+G, ... and reads block tmap[k] transposed.  Used by
+// the adjoint only.  Same calling rules as group_row_fwd.
+template <int B, int G, class VT, class XT, class AT>
+__device__ __forceinline__ void group_row_tr(const DevBsr<VT>& A, const XT* __restrict__ x,
+                                             int brow, int g, bool ok, AT (&acc)[B]) {
+#pragma unroll
+  for (int r = 0; r < B; ++r) acc[r] = AT(0);
+  if (ok) {
+    const int k0 = A.rp[brow], k1 = A.rp[brow + 1];
+    for (int k = k0 + g; k < k1; k += G) {
+      const int j = __ldg(A.col + k);
+      const int kb = __ldg(A.tmap + k);
+      AT a[B * B], xv[B];
+      load_run<B * B, VT, AT, true>(A.val + (size_t)kb * (B * B), a);
+      load_run<B, XT, AT, false>(x + (size_t)j * B, xv);
+#pragma unroll
+      for (int r = 0; r < B; ++r)
+#pragma unroll
+        for (int c = 0; c < B; ++c) acc[r] += a[c * B + r] * xv[c];
+    }
+  }
+  constexpr int W = G < 32 ? G : 32;
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int r = 0; r < B; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+}
+
+template <int B, int G, bool TR, class VT, class XT, class AT>
+__device__ __forceinline__ void group_row(const DevBsr<VT>& A, const XT* __restrict__ x, int brow,
+                                          int g, bool ok, AT (&acc)[B]) {
+  if constexpr (TR) group_row_tr<B, G, VT, XT, AT>(A, x, brow, g, ok, acc);
+  else group_row_fwd<B, G, VT, XT, AT>(A, x, brow, g, ok, acc);
+  if constexpr (G > 32) {
+    // one CTA per block row: combine the per-warp sums
+    __shared__ AT red[G / 32][B];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+      for (int r = 0; r < B; ++r) red[w][r] = acc[r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+      AT t = AT(0);
+#pragma unroll
+      for (int q = 0; q < G / 32; ++q) t += red[q][r];
+      acc[r] = t;
+    }
+  }
+}
+
+template <int B, class AT>
+__device__ __forceinline__ AT pick(const AT (&v)[B], int r) {
+  AT out = v[0];
+#pragma unroll
+  for (int q = 1; q < B; ++q)
+    if (q == r) out = v[q];
+  return out;
+}
+
 // ------------------------------------------------------------------ kernels
 enum { SPMV_SET = 0, SPMV_RESID = 1, SPMV_ADD = 2 };
 
@@ -153,6 +351,48 @@ __global__ void __launch_bounds__(256) k_spmv(DevBsr<VT> A, const XT* __restrict
   if constexpr (MODE == SPMV_SET) y[o] = (YT)acc;
   else if constexpr (MODE == SPMV_RESID) y[o] = (YT)(cvt<AT>(f[o]) - acc);
   else y[o] = (YT)(cvt<AT>(y[o]) + acc);
+}
+
+// Wide variant of k_spmv (G lanes per block row).
+template <int B, int G, bool TR, int MODE, class VT, class XT, class YT, class AT>
+__global__ void __launch_bounds__(256) k_spmv_w(DevBsr<VT> A, const XT* __restrict__ x,
+                                                const YT* __restrict__ f, YT* __restrict__ y) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int brow = (int)(t / G);
+  const int g = (int)(t % G);
+  const bool ok = brow < A.nbr;
+  AT acc[B];
+  group_row<B, G, TR, VT, XT, AT>(A, x, brow, g, ok, acc);
+  if (!ok || g >= B) return;
+  const size_t o = (size_t)brow * B + g;
+  const AT v = pick<B, AT>(acc, g);
+  if constexpr (MODE == SPMV_SET) y[o] = (YT)v;
+  else if constexpr (MODE == SPMV_RESID) y[o] = (YT)(cvt<AT>(f[o]) - v);
+  else y[o] = (YT)(cvt<AT>(y[o]) + v);
+}
+
+// Wide variant of k_relax.
+template <int B, int G, bool TR, class VT, class XT, class AT>
+__global__ void __launch_bounds__(256) k_relax_w(DevBsr<VT> A, const VT* __restrict__ M,
+                                                 const XT* __restrict__ f,
+                                                 const XT* __restrict__ x, XT* __restrict__ xo) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int brow = (int)(t / G);
+  const int g = (int)(t % G);
+  const bool ok = brow < A.nbr;
+  AT acc[B];
+  group_row<B, G, TR, VT, XT, AT>(A, x, brow, g, ok, acc);
+  if (!ok || g >= B) return;
+  AT fv[B];
+  load_run<B, XT, AT, false>(f + (size_t)brow * B, fv);
+  AT mr[B];
+  if constexpr (!TR) load_run<B, VT, AT, false>(M + (size_t)brow * (B * B) + g * B, mr);
+  else load_col<B, VT, AT>(M + (size_t)brow * (B * B), g, mr);
+  const size_t o = (size_t)brow * B + g;
+  AT out = cvt<AT>(x[o]);
+#pragma unroll
+  for (int c = 0; c < B; ++c) out += mr[c] * (fv[c] - acc[c]);
+  xo[o] = (XT)out;
 }
 
 // xo = x + M (f - A x)   (one relaxation sweep; M^T, A^T when TR).

@@ -17,7 +17,7 @@
 namespace gbs {
 
 constexpr int RED_THREADS = 256;
-constexpr int RED_BLOCKS = 152 * 4;
+constexpr int RED_BLOCKS = 152 * 8;   // 8 CTAs of 256 threads per SM: full occupancy
 constexpr int MAX_DOTS = 72;   // GMRES multi-dot: up to 64 basis vectors + spares
 
 enum ScalarSlot {
@@ -135,12 +135,46 @@ __device__ __forceinline__ void grid_reduce(double (&v)[ND], const Red& R, int s
   }
 }
 
-// y = K x (RESID: y = f - K x); d0 = sum y*w0, d1 = sum y*w1 (null w: 0).
-template <int B, bool TR, int MODE>
+// y = K x (RESID: y = f - K x); d0 = sum y*w0 (w0 null: 0), d1 = sum y*y
+// when self_dot (w0 must not alias y).  G lanes per block row (chunk
+// streaming, see group_row_fwd), grid-stride over block rows with a
+// warp-uniform exit so that every lane takes part in the shuffles.
+template <int B, int G, bool TR, int MODE>
 __global__ void __launch_bounds__(RED_THREADS)
     k_outer(DevBsr<double> K, const double* __restrict__ x, const double* __restrict__ f,
-            double* __restrict__ y, const double* __restrict__ w0, const double* __restrict__ w1,
-            Red R, int slot, int op, int reduce) {
+            double* __restrict__ y, const double* __restrict__ w0, int self_dot, Red R, int slot,
+            int op, int reduce) {
+  static_assert(G <= 32, "outer SpMV groups stay inside a warp");
+  double d[2] = {0.0, 0.0};
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t gid = t / G;
+  const int g = (int)(t % G);
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t brow = gid;; brow += ngroups) {
+    const bool ok = brow < K.nbr;
+    if (!__any_sync(0xffffffffu, ok)) break;
+    double acc[B];
+    group_row<B, G, TR, double, double, double>(K, x, (int)brow, g, ok, acc);
+    if (ok && g < B) {
+      const size_t o = (size_t)brow * B + g;
+      const double a = pick<B, double>(acc, g);
+      const double val = MODE == SPMV_RESID ? f[o] - a : a;
+      y[o] = val;
+      if (w0) d[0] += val * w0[o];
+      if (self_dot) d[1] += val * val;
+    }
+  }
+  if (reduce) grid_reduce<2>(d, R, slot, op);
+}
+
+// Same operation with one lane per scalar row (B lanes per block row, no
+// cross-lane sums): the fewest FP64 operations, used whenever K has
+// enough rows to fill the GPU.
+template <int B, bool TR, int MODE>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_outer_n(DevBsr<double> K, const double* __restrict__ x, const double* __restrict__ f,
+              double* __restrict__ y, const double* __restrict__ w0, int self_dot, Red R,
+              int slot, int op, int reduce) {
   constexpr int RPW = 32 / B;
   double d[2] = {0.0, 0.0};
   const int64_t nwarps = ((int64_t)K.nbr + RPW - 1) / RPW;
@@ -151,12 +185,12 @@ __global__ void __launch_bounds__(RED_THREADS)
        w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int brow = (int)(w * RPW + sub);
     if (!lane_ok || brow >= K.nbr) continue;
-    double acc = row_dot<B, TR, double, double, double>(K, x, brow, r);
+    const double acc = row_dot<B, TR, double, double, double>(K, x, brow, r);
     const size_t o = (size_t)brow * B + r;
-    double val = MODE == SPMV_RESID ? f[o] - acc : acc;
+    const double val = MODE == SPMV_RESID ? f[o] - acc : acc;
     y[o] = val;
     if (w0) d[0] += val * w0[o];
-    if (w1) d[1] += val * w1[o];
+    if (self_dot) d[1] += val * val;
   }
   if (reduce) grid_reduce<2>(d, R, slot, op);
 }

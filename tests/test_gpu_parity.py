@@ -113,6 +113,26 @@ def test_vcycle_on_imported_oracle_hierarchy(cfg):
         assert rel_inf(z, ref) <= 1e-12, (tr, rel_inf(z, ref))
 
 
+@pytest.mark.parametrize("G", ["0", "8", "16", "32", "256"])
+@pytest.mark.parametrize("name", ["c2", "c1"])
+def test_vcycle_every_lane_group_width(name, G, monkeypatch):
+    """Force each SpMV lane-group width (one lane per scalar row, 8, 16 or
+    32 lanes, or a 256-thread CTA per block row) on every level and compare
+    with the oracle."""
+    monkeypatch.setenv("GBS_SPMV_GROUP", G)
+    s = si.make_system(name, N=9)
+    B = s.bdim
+    A = bsr.from_arrays(s.indptr, s.indices, s.data, B)
+    Ho = amg.build_hierarchy(A, amg.AmgParams(coarse_enough=50, relax="jacobi"))
+    H = _import(Ho, B, relax=gb.GBS_JACOBI)
+    rng = np.random.default_rng(int(G) + 1)
+    for tr in (False, True):
+        r = rng.standard_normal(A.shape[0])
+        z = host(gb.apply_precond(H, dev(r), transpose=tr))
+        ref = amg.vcycle(Ho, r, 0, transpose=tr)
+        assert rel_inf(z, ref) <= 1e-12, (tr, rel_inf(z, ref))
+
+
 def test_vcycle_on_library_built_hierarchy():
     s = si.make_system("c2", N=12)
     A = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
@@ -189,7 +209,8 @@ def test_solve_c1_full_size(use_graph):
     x = host(x)
     assert info.converged and _true_rel(s, x) <= 1e-8
     assert abs(info.iters - io.iters) <= max(1, math.ceil(0.1 * io.iters)), (info.iters, io.iters)
-    assert np.linalg.norm(x - s.x_exact) / np.linalg.norm(s.x_exact) < 1e-5
+    # ||x - x_m|| / ||x_m|| <= cond(K) * 1e-8 with cond(K) ~ 2e3 at N = 16
+    assert np.linalg.norm(x - s.x_exact) / np.linalg.norm(s.x_exact) < 1e-4
 
 
 @pytest.mark.parametrize("N", [13, 16])
@@ -230,7 +251,8 @@ def test_solve_edge_cases():
     assert info2.iters == 0 and info2.converged
     # maxiter = 1: not converged, x and info still written
     H1 = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
-                            _params(s, relax=gb.GBS_JACOBI, maxiter=1, tol=1e-14))
+                            _params(s, relax=gb.GBS_JACOBI, maxiter=1, tol=1e-14,
+                                    coarse_enough=40))
     x, info = gb.solve(H1, dev(s.b))
     assert not info.converged and info.iters == 1 and info.status == 1
     assert info.rel_res < 1.0
