@@ -143,9 +143,11 @@ void alloc_work(Handle& h, cudaStream_t s) {
     case 3: h.K.G = choose_group<3, double, double>(h.Kh.nbr, h.Kh.nnzb()); break;
     default: h.K.G = choose_group<4, double, double>(h.Kh.nbr, h.Kh.nnzb()); break;
   }
+  if (h.K.G == 256) h.K.G = 32;  // the outer SpMV keeps lane groups inside a warp
   if (const char* e = std::getenv("GBS_SPMV_GROUP")) {  // tuning override
     int g = std::atoi(e);
     if (g == 0 || g == 8 || g == 16 || g == 32) h.K.G = g;
+    if (h.K.G == 256) h.K.G = 32;
   }
   if (h.prm.enable_adjoint) {
     std::vector<int32_t> tm;
@@ -189,7 +191,7 @@ void outer_B(const Handle& h, const double* x, const double* f, double* y, const
 #define GBS_OUT(BB)                                                                        \
   switch (h.K.G) {                                                                         \
     case 0:                                                                                \
-      k_outer_n<BB, TR, MODE><<<RED_BLOCKS, RED_THREADS, 0, s>>>(h.K, x, f, y, w0, self_dot, R, \
+      k_outer_n<BB, TR, MODE><<<OUTER_N_BLOCKS, RED_THREADS, 0, s>>>(h.K, x, f, y, w0, self_dot, R, \
                                                                   slot, op, reduce);       \
       break;                                                                               \
     case 8: GBS_OUTG(BB, 8); break;                                                        \

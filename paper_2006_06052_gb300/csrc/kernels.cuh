@@ -124,7 +124,7 @@ __device__ __forceinline__ AT row_dot(const DevBsr<VT>& A, const XT* __restrict_
                                       int r) {
   AT acc = AT(0);
   const int k0 = A.rp[brow], k1 = A.rp[brow + 1];
-#pragma unroll 2
+#pragma unroll 4
   for (int k = k0; k < k1; ++k) {
     const int j = __ldg(A.col + k);
     AT a[B], xv[B];
@@ -174,10 +174,9 @@ inline int choose_group(int64_t nbr, int64_t nnzb) {
   const double avg = nbr ? (double)nnzb / nbr : 0.0;
   const double chunks = avg * (Gm::FIXED ? Gm::LPB : B * B);
   if (sizeof(AT) == 8) {
-    if (nbr * B >= 65536 || avg < 4.0) return 0;
-    if (chunks <= 96) return 8;
-    if (chunks <= 384 || nbr > 2048) return 16;
-    return 32;
+    if (avg < 40.0) return 0;
+    if (nbr > 1024) return 32;
+    return 256;
   }
   if (chunks <= 48) return 8;
   if (chunks <= 96) return 16;

@@ -18,6 +18,7 @@ namespace gbs {
 
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 152 * 8;   // 8 CTAs of 256 threads per SM: full occupancy
+constexpr int OUTER_N_BLOCKS = 152 * 4;  // one-lane-per-row FP64 SpMV: FP64-pipe bound, half occupancy is faster
 constexpr int MAX_DOTS = 72;   // GMRES multi-dot: up to 64 basis vectors + spares
 
 enum ScalarSlot {
