@@ -70,6 +70,8 @@ DevBsr<VT> upload_bsr(Arena& ar, const HBsr& H, bool with_tmap, cudaStream_t s,
   d.col = ar.upload(H.col.data(), H.col.size(), s);
   keep.push_back(cast_vec<VT>(H.val));
   d.val = ar.upload(keep.back().data(), keep.back().size(), s);
+  if (H.nnzb() * H.br * H.bc >= (int64_t)INT32_MAX)
+    throw SetupError{"a level holds 2^31 or more block values (int32 element indices)"};
   switch (H.br) {
     case 1: d.G = choose_group<1, VT, AT>(H.nbr, H.nnzb()); break;
     case 2: d.G = choose_group<2, VT, AT>(H.nbr, H.nnzb()); break;

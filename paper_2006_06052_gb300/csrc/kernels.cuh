@@ -40,6 +40,7 @@ __device__ __forceinline__ float to_f(double v) { return (float)v; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 template <class AT, class T>
 __device__ __forceinline__ AT cvt(T v);
+template <> __device__ __forceinline__ int cvt<int, int>(int v) { return v; }
 template <> __device__ __forceinline__ double cvt<double, double>(double v) { return v; }
 template <> __device__ __forceinline__ double cvt<double, float>(float v) { return (double)v; }
 template <> __device__ __forceinline__ float cvt<float, float>(float v) { return v; }
@@ -155,7 +156,9 @@ struct Geom {
   static constexpr int CB = BB % 16 == 0 ? 16 : (BB % 8 == 0 ? 8 : (BB % 4 == 0 ? 4 : (int)sizeof(VT)));
   static constexpr int E = CB / (int)sizeof(VT);   // values per chunk
   static constexpr int LPB = BB / CB;              // chunks per block
-  static constexpr bool FIXED = (LPB & (LPB - 1)) == 0 && LPB <= 8 && (E <= B ? B % E == 0 : E % B == 0);
+  static constexpr bool FIXED = CB == 16 && (LPB & (LPB - 1)) == 0 && LPB <= 8 &&
+                                (E <= B ? B % E == 0 : E % B == 0);
+  static constexpr int E16 = 16 / (int)sizeof(VT);  // values per aligned 16-byte chunk
   static constexpr int NR = E > B ? E / B : 1;     // rows touched by one chunk
   static constexpr int NX = E > B ? B : E;         // x entries one chunk needs
 };
@@ -176,6 +179,16 @@ inline int choose_group(int64_t nbr, int64_t nnzb) {
   if (sizeof(AT) == 8) {
     if (avg < 40.0) return 0;
     if (nbr > 1024) return 32;
+    return 256;
+  }
+  if (!Gm::FIXED) {
+    // aligned-chunk streaming (two chunks per lane per batch) pays index
+    // work per value: short rows stay one lane per scalar row
+    if (avg < 40.0) return 0;
+    const double c16 = avg * Gm::BB / 16.0;
+    if (c16 <= 16) return 8;
+    if (c16 <= 32) return 16;
+    if (c16 <= 64 || nbr > 4096) return 32;
     return 256;
   }
   if (chunks <= 48) return 8;
@@ -239,29 +252,82 @@ __device__ __forceinline__ void group_row_fwd(const DevBsr<VT>& A, const XT* __r
         for (int q = 0; q < Gm::NR; ++q)
           if (r == r0 + q) acc[r] += part[q];
     } else {
-      const int ne = (k1 - k0) * (B * B);
-      constexpr int U = 4;
-      for (int eb = g; eb < ne; eb += U * G) {
-        int j[U], rr[U], cl[U], ee[U];
-        AT v[U];
+      // Aligned-chunk streaming (B = 3, or blocks smaller than 16 bytes):
+      // lanes take the 16-byte-aligned chunks of the global value array that
+      // overlap this row's values [e0, e1) and skip the values outside it.
+      // Element indices fit in int32 (checked at upload: nnzb*B*B < 2^31).
+      constexpr int BB = B * B;
+      constexpr int EC = Gm::E16;
+      const int e0 = k0 * BB, e1 = k1 * BB;
+      const int cfirst = e0 / EC, clast = (e1 - 1) / EC;
+      constexpr int U = 2;
+      for (int cb = cfirst + g; cb <= clast; cb += U * G) {
+        AT v[U][EC];
+        int cc[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          ee[u] = min(eb + u * G, ne - 1);
-          const int kb = ee[u] / (B * B);
-          const int w = ee[u] - kb * (B * B);
-          rr[u] = w / B;
-          cl[u] = w - rr[u] * B;
-          j[u] = __ldg(A.col + k0 + kb);
+          cc[u] = min(cb + u * G, clast);
+          load_run<EC, VT, AT, true>(A.val + (size_t)cc[u] * EC, v[u]);
         }
+        if constexpr (B == 1) {
+          // scalar CSR: the chunk's EC column indices are contiguous too
+          int j[U][EC];
 #pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = cvt<AT>(__ldcs(vrow + ee[u]));
+          for (int u = 0; u < U; ++u) load_run<EC, int, int, false>(A.col + (size_t)cc[u] * EC, j[u]);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const AT xv = cvt<AT>(__ldg(x + (size_t)j[u] * B + cl[u]));
-          if (eb + u * G < ne) {
+          for (int u = 0; u < U; ++u) {
+            if (cb + u * G > clast) continue;
 #pragma unroll
-            for (int q = 0; q < B; ++q)
-              if (q == rr[u]) acc[q] += v[u] * xv;
+            for (int q = 0; q < EC; ++q) {
+              const int e = cc[u] * EC + q;
+              const AT xv = cvt<AT>(__ldg(x + j[u][q]));
+              if (e >= e0 && e < e1) acc[0] += v[u][q] * xv;
+            }
+          }
+        } else if constexpr (EC <= BB) {
+          // a chunk spans at most two blocks: fetch both blocks' x once
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            if (cb + u * G > clast) continue;
+            const int ef = cc[u] * EC;
+            const int kba = ef / BB;
+            const int kbb = min((ef + EC - 1) / BB, k1 - 1);
+            AT xa[B], xb[B];
+            load_run<B, XT, AT, false>(x + (size_t)__ldg(A.col + max(kba, k0)) * B, xa);
+            load_run<B, XT, AT, false>(x + (size_t)__ldg(A.col + kbb) * B, xb);
+#pragma unroll
+            for (int q = 0; q < EC; ++q) {
+              const int e = ef + q;
+              const int kb = e / BB;
+              const int w = e - kb * BB;
+              const int r = w / B, c = w - r * B;
+              AT xv = AT(0);
+#pragma unroll
+              for (int t = 0; t < B; ++t)
+                if (t == c) xv = (kb == kba) ? xa[t] : xb[t];
+              const AT pv = (e >= e0 && e < e1) ? v[u][q] * xv : AT(0);
+#pragma unroll
+              for (int t = 0; t < B; ++t)
+                if (t == r) acc[t] += pv;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            if (cb + u * G > clast) continue;
+#pragma unroll
+            for (int q = 0; q < EC; ++q) {
+              const int e = cc[u] * EC + q;
+              if (e < e0 || e >= e1) continue;
+              const int kb = e / BB;
+              const int w = e - kb * BB;
+              const int r = w / B, c = w - r * B;
+              const int j = __ldg(A.col + kb);
+              const AT pv = v[u][q] * cvt<AT>(__ldg(x + (size_t)j * B + c));
+#pragma unroll
+              for (int t = 0; t < B; ++t)
+                if (t == r) acc[t] += pv;
+            }
           }
         }
       }
@@ -341,7 +407,7 @@ enum { SPMV_SET = 0, SPMV_RESID = 1, SPMV_ADD = 2 };
 
 // MODE SET: y = A x;  RESID: y = f - A x;  ADD: y += A x.
 template <int B, bool TR, int MODE, class VT, class XT, class YT, class AT>
-__global__ void __launch_bounds__(256) k_spmv(DevBsr<VT> A, const XT* __restrict__ x,
+__global__ void __launch_bounds__(256, 4) k_spmv(DevBsr<VT> A, const XT* __restrict__ x,
                                               const YT* __restrict__ f, YT* __restrict__ y) {
   RowMap<B> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   if (!m.lane_ok || m.brow >= A.nbr) return;
@@ -354,7 +420,7 @@ __global__ void __launch_bounds__(256) k_spmv(DevBsr<VT> A, const XT* __restrict
 
 // Wide variant of k_spmv (G lanes per block row).
 template <int B, int G, bool TR, int MODE, class VT, class XT, class YT, class AT>
-__global__ void __launch_bounds__(256) k_spmv_w(DevBsr<VT> A, const XT* __restrict__ x,
+__global__ void __launch_bounds__(256, 4) k_spmv_w(DevBsr<VT> A, const XT* __restrict__ x,
                                                 const YT* __restrict__ f, YT* __restrict__ y) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int brow = (int)(t / G);
@@ -372,7 +438,7 @@ __global__ void __launch_bounds__(256) k_spmv_w(DevBsr<VT> A, const XT* __restri
 
 // Wide variant of k_relax.
 template <int B, int G, bool TR, class VT, class XT, class AT>
-__global__ void __launch_bounds__(256) k_relax_w(DevBsr<VT> A, const VT* __restrict__ M,
+__global__ void __launch_bounds__(256, 4) k_relax_w(DevBsr<VT> A, const VT* __restrict__ M,
                                                  const XT* __restrict__ f,
                                                  const XT* __restrict__ x, XT* __restrict__ xo) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -396,7 +462,7 @@ __global__ void __launch_bounds__(256) k_relax_w(DevBsr<VT> A, const VT* __restr
 
 // xo = x + M (f - A x)   (one relaxation sweep; M^T, A^T when TR).
 template <int B, bool TR, class VT, class XT, class AT>
-__global__ void __launch_bounds__(256) k_relax(DevBsr<VT> A, const VT* __restrict__ M,
+__global__ void __launch_bounds__(256, 4) k_relax(DevBsr<VT> A, const VT* __restrict__ M,
                                                const XT* __restrict__ f,
                                                const XT* __restrict__ x, XT* __restrict__ xo) {
   RowMap<B> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
@@ -419,7 +485,7 @@ __global__ void __launch_bounds__(256) k_relax(DevBsr<VT> A, const VT* __restric
 
 // x = M f   (zero-guess smoothing step).
 template <int B, bool TR, class VT, class XT, class AT>
-__global__ void __launch_bounds__(256) k_mapply(int nbr, const VT* __restrict__ M,
+__global__ void __launch_bounds__(256, 4) k_mapply(int nbr, const VT* __restrict__ M,
                                                 const XT* __restrict__ f, XT* __restrict__ x) {
   RowMap<B> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   if (!m.lane_ok || m.brow >= nbr) return;
@@ -435,7 +501,7 @@ __global__ void __launch_bounds__(256) k_mapply(int nbr, const VT* __restrict__ 
 
 // x = Ainv f, dense n x n row-major, one warp per row.
 template <class VT, class XT, class AT>
-__global__ void __launch_bounds__(256) k_gemv(int n, const VT* __restrict__ Ainv,
+__global__ void __launch_bounds__(256, 4) k_gemv(int n, const VT* __restrict__ Ainv,
                                               const XT* __restrict__ f, XT* __restrict__ x) {
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;

@@ -141,7 +141,7 @@ __device__ __forceinline__ void grid_reduce(double (&v)[ND], const Red& R, int s
 // streaming, see group_row_fwd), grid-stride over block rows with a
 // warp-uniform exit so that every lane takes part in the shuffles.
 template <int B, int G, bool TR, int MODE>
-__global__ void __launch_bounds__(RED_THREADS)
+__global__ void __launch_bounds__(RED_THREADS, 4)
     k_outer(DevBsr<double> K, const double* __restrict__ x, const double* __restrict__ f,
             double* __restrict__ y, const double* __restrict__ w0, int self_dot, Red R, int slot,
             int op, int reduce) {
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(RED_THREADS)
 // cross-lane sums): the fewest FP64 operations, used whenever K has
 // enough rows to fill the GPU.
 template <int B, bool TR, int MODE>
-__global__ void __launch_bounds__(RED_THREADS)
+__global__ void __launch_bounds__(RED_THREADS, 4)
     k_outer_n(DevBsr<double> K, const double* __restrict__ x, const double* __restrict__ f,
               double* __restrict__ y, const double* __restrict__ w0, int self_dot, Red R,
               int slot, int op, int reduce) {
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(RED_THREADS)
 }
 
 // p = r + beta (p - omega v), beta = (rho / rho_old) (alpha / omega); p = r on the first step.
-__global__ void k_bicg_p(int64_t n, const double* __restrict__ r, const double* __restrict__ v,
+static __global__ void k_bicg_p(int64_t n, const double* __restrict__ r, const double* __restrict__ v,
                          double* __restrict__ p, const double* __restrict__ sc) {
   const bool first = sc[S_FIRST] != 0.0;
   const double omega = sc[S_OMEGA];
@@ -208,7 +208,7 @@ __global__ void k_bicg_p(int64_t n, const double* __restrict__ r, const double* 
 }
 
 // s = r - alpha v
-__global__ void k_bicg_s(int64_t n, const double* __restrict__ r, const double* __restrict__ v,
+static __global__ void k_bicg_s(int64_t n, const double* __restrict__ r, const double* __restrict__ v,
                          double* __restrict__ s, const double* __restrict__ sc) {
   const double alpha = sc[S_ALPHA];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -217,7 +217,7 @@ __global__ void k_bicg_s(int64_t n, const double* __restrict__ r, const double* 
 }
 
 // x += alpha phat + omega shat; r = s - omega t; d0 = rhat.r, d1 = r.r
-__global__ void __launch_bounds__(RED_THREADS)
+static __global__ void __launch_bounds__(RED_THREADS, 4)
     k_bicg_xr(int64_t n, double* __restrict__ x, const double* __restrict__ ph,
               const double* __restrict__ sh, const double* __restrict__ s,
               const double* __restrict__ t, double* __restrict__ r,
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(RED_THREADS)
 }
 
 // d0 = a.b, d1 = c.c (c may be null)
-__global__ void __launch_bounds__(RED_THREADS)
+static __global__ void __launch_bounds__(RED_THREADS, 4)
     k_dot2(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
            const double* __restrict__ c, Red R, int slot, int op) {
   double d[2] = {0.0, 0.0};
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(RED_THREADS)
   grid_reduce<2>(d, R, slot, op);
 }
 
-__global__ void k_set_restart(double* sc) {
+static __global__ void k_set_restart(double* sc) {
   sc[S_RHO] = sc[S_RR];
   sc[S_RHO_OLD] = 1.0;
   sc[S_ALPHA] = 1.0;
@@ -259,7 +259,7 @@ __global__ void k_set_restart(double* sc) {
 // ------------------------------------------------------------------ GMRES
 // h[i] = V_i . w for i < J (chunks of 8 vectors), and sc[S_WW0] = w . w.
 // gate: if non-null and *gate == 0 the kernel does nothing.
-__global__ void __launch_bounds__(RED_THREADS)
+static __global__ void __launch_bounds__(RED_THREADS, 4)
     k_multidot(int64_t n, const double* __restrict__ V, int J, const double* __restrict__ w,
                double* __restrict__ h, Red R, int slot, const double* __restrict__ gate) {
   if (gate && *gate == 0.0) return;
@@ -318,9 +318,58 @@ __global__ void __launch_bounds__(RED_THREADS)
   if (threadIdx.x == 0) R.counter[slot] = 0u;
 }
 
+// Single-pass multi-dot for J <= JM: every thread reads w once and keeps
+// all J partial dots (plus w.w) in registers.  Same outputs as k_multidot.
+template <int JM>
+static __global__ void __launch_bounds__(RED_THREADS, 2)
+    k_multidot1(int64_t n, const double* __restrict__ V, int J, const double* __restrict__ w,
+                double* __restrict__ h, Red R, int slot, const double* __restrict__ gate) {
+  if (gate && *gate == 0.0) return;
+  double v[JM + 1];
+#pragma unroll
+  for (int q = 0; q <= JM; ++q) v[q] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+#pragma unroll
+    for (int q = 0; q < JM; ++q)
+      if (q < J) v[q] += V[(size_t)q * n + i] * wi;
+    v[JM] += wi * wi;
+  }
+  __shared__ double sh[RED_THREADS / 32][JM + 1];
+  __shared__ bool last;
+  block_sum<JM + 1>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < JM; ++q)
+      if (q < J) R.partials[(size_t)blockIdx.x * MAX_DOTS + q] = v[q];
+    R.partials[(size_t)blockIdx.x * MAX_DOTS + J] = v[JM];
+    __threadfence();
+    unsigned t = atomicAdd(R.counter + slot, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // the last block: reduce column q of the partials in block order
+  for (int q = threadIdx.x >> 5; q <= J; q += RED_THREADS / 32) {
+    double acc = 0.0;
+    for (int b = threadIdx.x & 31; b < (int)gridDim.x; b += 32)
+      acc += __ldcg(R.partials + (size_t)b * MAX_DOTS + q);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) {
+      if (q < J) h[q] = acc;
+      else R.sc[S_WW0] = acc;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) R.counter[slot] = 0u;
+}
+
 // w -= sum_i h[i] V_i; sc[S_WW] = w.w; sc[S_REORTH] = (ww < 0.5 ww0).
 // accumulate (non-null): hacc[i] += h[i] as well (second pass).
-__global__ void __launch_bounds__(RED_THREADS)
+static __global__ void __launch_bounds__(RED_THREADS, 4)
     k_orth(int64_t n, const double* __restrict__ V, int J, double* __restrict__ w,
            const double* __restrict__ h, double* __restrict__ hacc, Red R, int slot,
            const double* __restrict__ gate) {
@@ -364,7 +413,7 @@ __global__ void __launch_bounds__(RED_THREADS)
 }
 
 // w /= sqrt(sc[S_WW]) (if nonzero); hnext = sqrt(sc[S_WW])
-__global__ void k_normalize(int64_t n, double* __restrict__ w, const double* __restrict__ sc,
+static __global__ void k_normalize(int64_t n, double* __restrict__ w, const double* __restrict__ sc,
                             double* __restrict__ hnext) {
   const double nrm = sqrt(sc[S_WW]);
   if (blockIdx.x == 0 && threadIdx.x == 0) *hnext = nrm;
@@ -376,7 +425,7 @@ __global__ void k_normalize(int64_t n, double* __restrict__ w, const double* __r
 }
 
 // v = r / sqrt(sc[S_RR])
-__global__ void k_scale_rr(int64_t n, const double* __restrict__ r, double* __restrict__ v,
+static __global__ void k_scale_rr(int64_t n, const double* __restrict__ r, double* __restrict__ v,
                            const double* __restrict__ sc) {
   const double inv = 1.0 / sqrt(sc[S_RR]);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -385,7 +434,7 @@ __global__ void k_scale_rr(int64_t n, const double* __restrict__ r, double* __re
 }
 
 // u = sum_{i<J} y[i] V_i
-__global__ void k_combine(int64_t n, const double* __restrict__ V, int J,
+static __global__ void k_combine(int64_t n, const double* __restrict__ V, int J,
                           const double* __restrict__ y, double* __restrict__ u) {
   __shared__ double ys[MAX_DOTS];
   for (int i = threadIdx.x; i < J; i += blockDim.x) ys[i] = y[i];
@@ -398,7 +447,7 @@ __global__ void k_combine(int64_t n, const double* __restrict__ V, int J,
   }
 }
 
-__global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+static __global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     y[i] += a * x[i];
