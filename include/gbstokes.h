@@ -202,6 +202,33 @@ gbs_status gbs_import_hierarchy(const gbs_bsr* A, const gbs_bsr* P, const gbs_bs
  * replayed CUDA graph counts each of its kernel nodes).  Telemetry only. */
 int64_t gbs_kernel_launches(void);
 
+/* y = A x, dots[0] = w . y (0 if w is NULL) and dots[1] = y . y for an FP64
+ * block-CSR matrix held in DEVICE memory, without allocating anything.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they need the operation -- code
+ * running inside CUDA graph capture (allocation cannot be captured), or
+ * applications whose own memory manager owns the device.  Its reduction
+ * scratch (two doubles per CTA of a fixed 608-CTA grid plus a counter,
+ * 9.7 KB) is a file-scope __device__ array that every GPU loading the
+ * library holds until the process exits; the grid never grows with the
+ * matrix, so any matrix fits, and sizes beyond the int32 index range
+ * (nnzb, n_brows*bdim, n_bcols*bdim > 2^31-1) are rejected with
+ * GBS_ERR_INVALID.
+ * row_ptr int32[n_brows+1], col_idx int32[nnzb] (sorted, < n_bcols), vals
+ * f64[nnzb*bdim*bdim] row-major blocks, x f64[n_bcols*bdim], y
+ * f64[n_brows*bdim], w f64[n_brows*bdim] or NULL, dots f64[2]: all device
+ * pointers, caller-owned; vals, x, y, w 16-byte aligned; w must not alias
+ * y.  The structure is not validated (it lives on the device).
+ * The first call on a device looks up the scratch address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one scratch array, so
+ * calls that overlap on the GPU (different streams, no ordering) race;
+ * each call clears the counter it needs.  Asynchronous on stream. */
+gbs_status gbs_spmv_dots_noalloc(int32_t n_brows, int32_t n_bcols, int32_t bdim, int64_t nnzb,
+                                 const int32_t* row_ptr, const int32_t* col_idx,
+                                 const double* vals, const double* x, double* y,
+                                 const double* w, double* dots, void* stream);
+
 /* Free everything the handle owns.  Synchronises the device. */
 gbs_status gbs_destroy(gbs_hierarchy* h);
 

@@ -20,7 +20,7 @@ from ._build import LIB as _LIB_PATH, build as _build_lib
 __all__ = [
     "GbsError", "Params", "Info", "Hierarchy", "params_default", "build_hierarchy",
     "import_hierarchy", "solve", "solve_adjoint", "sampled_outer", "update_values", "spmv",
-    "apply_precond", "hierarchy_info", "export_level", "export_level_sizes", "load_library", "build", "kernel_launches",
+    "apply_precond", "hierarchy_info", "export_level", "export_level_sizes", "spmv_dots_noalloc", "load_library", "build", "kernel_launches",
     "GBS_PC_AMG", "GBS_PC_SCHUR", "GBS_BICGSTAB", "GBS_GMRES", "GBS_FP64", "GBS_FP32",
     "GBS_BF16", "GBS_SPAI0", "GBS_JACOBI", "EXPORTED",
 ]
@@ -39,7 +39,7 @@ EXPORTED = [
     "gbs_params_default", "gbs_build_hierarchy", "gbs_solve", "gbs_solve_adjoint",
     "gbs_sampled_outer", "gbs_update_values", "gbs_spmv", "gbs_apply_precond",
     "gbs_hierarchy_info", "gbs_export_level", "gbs_import_hierarchy", "gbs_destroy",
-    "gbs_last_error", "gbs_kernel_launches",
+    "gbs_last_error", "gbs_kernel_launches", "gbs_spmv_dots_noalloc",
 ]
 
 
@@ -121,6 +121,8 @@ def load_library():
         "gbs_import_hierarchy": [c.POINTER(_Bsr), c.POINTER(_Bsr), c.POINTER(_Bsr),
                                  c.POINTER(P), P, c.c_int32, c.POINTER(Params), P, c.POINTER(P)],
         "gbs_destroy": [P],
+        "gbs_spmv_dots_noalloc": [c.c_int32, c.c_int32, c.c_int32, c.c_int64, P, P, P, P, P, P,
+                                  P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -288,6 +290,28 @@ def sampled_outer(H: Hierarchy, lam, x, alpha=-1.0, grad=None, stream=None):
                                             _dptr(grad, H.nnzb * H.bdim ** 2, "grad"),
                                             _stream_ptr(stream)))
     return grad
+
+
+def spmv_dots_noalloc(row_ptr, col_idx, vals, bdim, x, y, w=None, dots=None, n_bcols=None,
+                      stream=None):
+    """y = A x and dots = [w.y, y.y] for a BSR matrix already in device memory
+    (torch CUDA tensors: int32 row_ptr/col_idx, float64 vals), through
+    gbs_spmv_dots_noalloc, which allocates nothing on the device."""
+    import torch
+    n_brows = row_ptr.numel() - 1
+    if dots is None:
+        dots = torch.zeros(2, dtype=torch.float64, device=x.device)
+    for t, nm in ((row_ptr, "row_ptr"), (col_idx, "col_idx")):
+        if not (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()):
+            raise TypeError("%s must be a contiguous CUDA int32 tensor" % nm)
+    nb = n_brows if n_bcols is None else n_bcols
+    _check(load_library().gbs_spmv_dots_noalloc(
+        n_brows, nb, bdim, col_idx.numel(), ctypes.c_void_p(row_ptr.data_ptr()),
+        ctypes.c_void_p(col_idx.data_ptr()), _dptr(vals, col_idx.numel() * bdim * bdim, "vals"),
+        _dptr(x, nb * bdim, "x"), _dptr(y, n_brows * bdim, "y"),
+        _dptr(w, n_brows * bdim, "w") if w is not None else None, _dptr(dots, 2, "dots"),
+        _stream_ptr(stream)))
+    return y, dots
 
 
 def update_values(H: Hierarchy, vals, stream=None):

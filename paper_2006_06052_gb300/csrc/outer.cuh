@@ -34,7 +34,8 @@ enum FinOp {
   FIN_REPLACE,     // rho = d0; rr = d1
   FIN_INIT,        // rhat = r: rho = rr = d1; rho_old = alpha = omega = 1; first = 1
   FIN_BB,          // bb = d0
-  FIN_RR           // rr = d1
+  FIN_RR,          // rr = d1
+  FIN_OUT          // sc[0] = d0, sc[1] = d1 (sc points at a caller's 2-double output)
 };
 
 struct Red {
@@ -74,6 +75,7 @@ __device__ __forceinline__ void finalize(int op, const double* d, double* sc) {
       break;
     case FIN_BB: sc[S_BB] = d[0]; break;
     case FIN_RR: sc[S_RR] = d[1]; break;
+    case FIN_OUT: sc[0] = d[0]; sc[1] = d[1]; break;
   }
 }
 
