@@ -64,6 +64,40 @@ def solver_params(gb, wl, **kw):
     return gb.params_default(relax=relax, precision=prec, enable_adjoint=0, **kw)
 
 
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate (nominal): ~2 DFMA per clock per SM at 2.07 GHz
+
+
+def kernel_source_sha1():
+    """Hash of the sources of the outer SpMV kernel (kernels.cuh + outer.cuh)."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("kernels.cuh", "outer.cuh"):
+        with open(os.path.join(ROOT, "paper_2006_06052_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per launch of the outer SpMV from the committed ncu summary
+    profiles/k_outer_n_<workload>.txt, or None when the kernel sources have
+    changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "k_outer_n_%s.txt" % workload)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("source_sha1") != kernel_source_sha1():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -360,14 +394,18 @@ def main():
     spmv_ms = e0.elapsed_time(e1) / reps
     spmv_bytes = algorithmic_spmv_bytes(nbr, nnzb, B)
     achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
-    traffic = None
-    tr_env = os.environ.get("GBS_SPMV_DRAM_BYTES")
-    if tr_env:
-        traffic = float(tr_env)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_outer (BSR %dx%d FP64 SpMV of K)" % (B, B),
-                "algorithmic_bytes": spmv_bytes, "ms": spmv_ms, "peak_kind": peak_kind}
+    traffic = profiled_traffic(wl)
+    # FP64 block SpMV does B*B FMAs per stored block; on GB300 the FP64 pipe
+    # (not HBM) is the tighter roofline for this kernel
+    flops = 2.0 * nnzb * B * B
+    tflops = flops / (spmv_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "k_outer_n (BSR %dx%d FP64 SpMV of K)" % (B, B),
+                "algorithmic_flops": flops, "ms": spmv_ms,
+                "peak_kind": "nominal FP64 rate (about 2 DFMA/clk/SM x 152 SMs x 2.07 GHz)",
+                "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "algorithmic_bytes": spmv_bytes, "peak_kind": peak_kind}}
     # the V-cycle as a whole (monolithic AMG only)
     vcycle = None
     if spec["system"] != "c3":
