@@ -73,6 +73,17 @@ DevBsr<VT> upload_bsr(Arena& ar, const HBsr& H, bool with_tmap, cudaStream_t s,
   if (H.nnzb() * H.br * H.bc >= (int64_t)INT32_MAX)
     throw SetupError{"a level holds 2^31 or more block values (int32 element indices)"};
   switch (H.br) {
+    case 1: d.S = choose_split<1>(H.nbr, H.nnzb()); break;
+    case 2: d.S = choose_split<2>(H.nbr, H.nnzb()); break;
+    case 3: d.S = choose_split<3>(H.nbr, H.nnzb()); break;
+    default: d.S = choose_split<4>(H.nbr, H.nnzb()); break;
+  }
+  if (const char* e = std::getenv("GBS_SPMV_SPLIT")) {  // tuning override: 1, 2, 4, 8
+    int sp = std::atoi(e);
+    if (sp == 1 || sp == 2 || sp == 4 || sp == 8) d.S = sp;
+  }
+  while (d.S > 1 && H.br * d.S > 32) d.S >>= 1;
+  switch (H.br) {
     case 1: d.G = choose_group<1, VT, AT>(H.nbr, H.nnzb()); break;
     case 2: d.G = choose_group<2, VT, AT>(H.nbr, H.nnzb()); break;
     case 3: d.G = choose_group<3, VT, AT>(H.nbr, H.nnzb()); break;
@@ -102,7 +113,16 @@ void spmv_B(const DevBsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s
     case 32: k_spmv_w<B, 32, TR, MODE, VT, XT, YT, AT><<<grid_for(nt), 256, 0, s>>>(A, x, f, y); break;
     case 256: k_spmv_w<B, 256, TR, MODE, VT, XT, YT, AT><<<grid_for(nt), 256, 0, s>>>(A, x, f, y); break;
     default:
-      k_spmv<B, TR, MODE, VT, XT, YT, AT><<<grid_for(row_threads<B>(A.nbr)), 256, 0, s>>>(A, x, f, y);
+      switch (A.S) {
+        case 2: k_spmv<B, 2, TR, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<B, 2>(A.nbr)), 256, 0, s>>>(A, x, f, y); break;
+        case 4:
+          if constexpr (B * 4 <= 32) k_spmv<B, 4, TR, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<B, 4>(A.nbr)), 256, 0, s>>>(A, x, f, y);
+          break;
+        case 8:
+          if constexpr (B * 8 <= 32) k_spmv<B, 8, TR, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<B, 8>(A.nbr)), 256, 0, s>>>(A, x, f, y);
+          break;
+        default: k_spmv<B, 1, TR, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<B, 1>(A.nbr)), 256, 0, s>>>(A, x, f, y);
+      }
   }
 }
 template <bool TR, int MODE, class VT, class XT, class YT, class AT>
@@ -125,7 +145,17 @@ void relax(int B, const DevBsr<VT>& A, const VT* M, const XT* f, const XT* x, XT
     case 16: k_relax_w<BB, 16, TR, VT, XT, AT><<<grid_for((int64_t)A.nbr * 16), 256, 0, s>>>(A, M, f, x, xo); break; \
     case 32: k_relax_w<BB, 32, TR, VT, XT, AT><<<grid_for((int64_t)A.nbr * 32), 256, 0, s>>>(A, M, f, x, xo); break; \
     case 256: k_relax_w<BB, 256, TR, VT, XT, AT><<<grid_for((int64_t)A.nbr * 256), 256, 0, s>>>(A, M, f, x, xo); break; \
-    default: k_relax<BB, TR, VT, XT, AT><<<grid_for(row_threads<BB>(A.nbr)), 256, 0, s>>>(A, M, f, x, xo);         \
+    default:                                                                                     \
+      switch (A.S) {                                                                             \
+        case 2: k_relax<BB, 2, TR, VT, XT, AT><<<grid_for(row_threads_s<BB, 2>(A.nbr)), 256, 0, s>>>(A, M, f, x, xo); break; \
+        case 4:                                                                                  \
+          if constexpr (BB * 4 <= 32) k_relax<BB, 4, TR, VT, XT, AT><<<grid_for(row_threads_s<BB, 4>(A.nbr)), 256, 0, s>>>(A, M, f, x, xo); \
+          break;                                                                                 \
+        case 8:                                                                                  \
+          if constexpr (BB * 8 <= 32) k_relax<BB, 8, TR, VT, XT, AT><<<grid_for(row_threads_s<BB, 8>(A.nbr)), 256, 0, s>>>(A, M, f, x, xo); \
+          break;                                                                                 \
+        default: k_relax<BB, 1, TR, VT, XT, AT><<<grid_for(row_threads_s<BB, 1>(A.nbr)), 256, 0, s>>>(A, M, f, x, xo); \
+      }                                                                                          \
   }
   switch (B) {
     case 1: GBS_RELAX(1); break;

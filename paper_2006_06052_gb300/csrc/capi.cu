@@ -438,14 +438,12 @@ gbs_status solve_gmres(Handle& h, const double* b, double* x, bool tr, cudaStrea
       h.pc->apply(h.V + (size_t)j * n, h.z, tr, s);
       outer(h, tr, SPMV_SET, h.z, nullptr, w, nullptr, 0, 0, FIN_STORE, false, s);
       const int J = j + 1;
-      if (J <= 32) k_multidot1<32><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol, h.red, 5, nullptr);
-      else k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol, h.red, 5, nullptr);
+      k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol, h.red, 5, nullptr);
       GBS_LAUNCH_CHECK();
       k_orth<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol, nullptr, h.red, 6, nullptr);
       GBS_LAUNCH_CHECK();
       const double* gate = h.sc + S_REORTH;
-      if (J <= 32) k_multidot1<32><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol2, h.red, 7, gate);
-      else k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol2, h.red, 7, gate);
+      k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol2, h.red, 7, gate);
       GBS_LAUNCH_CHECK();
       k_orth<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol2, h.hcol, h.red, 8, gate);
       GBS_LAUNCH_CHECK();

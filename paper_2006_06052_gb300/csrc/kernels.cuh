@@ -31,6 +31,7 @@ struct DevBsr {
   const VT* val = nullptr;
   const int* tmap = nullptr;  // transpose map (may be null)
   int G = 0;                  // lanes per block row (0: one lane per scalar row)
+  int S = 1;                  // G == 0: lanes sharing each scalar row (1, 2, 4, 8)
 };
 
 
@@ -119,14 +120,53 @@ inline int64_t row_threads(int nbr) {
   return (int64_t)((nbr + RPW - 1) / RPW) * 32;
 }
 
-// Row r of (A x) for block row `brow` (A x or A^T x through tmap).
-template <int B, bool TR, class VT, class XT, class AT>
+// Row split: S lanes share each scalar row (lane s of the row takes blocks
+// k0+s, k0+s+S, ...), B*S lanes per block row, 32/(B*S) block rows per
+// warp.  Their partial sums meet in a shuffle-down tree that costs one add
+// per step, so long rows get S-fold parallelism for log2(S) extra adds.
+template <int B, int S>
+struct RowMapS {
+  static constexpr int GL = B * S;
+  static constexpr int RPW = 32 / GL;
+  int brow, r, s, lane, base;
+  bool lane_ok;
+  __device__ __forceinline__ explicit RowMapS(int64_t gtid) {
+    const int64_t warp = gtid >> 5;
+    lane = (int)(gtid & 31);
+    const int sub = lane / GL;
+    const int q = lane - sub * GL;
+    s = q / B;
+    r = q - s * B;
+    base = sub * GL;
+    lane_ok = sub < RPW;
+    brow = (int)(warp * RPW + sub);
+  }
+};
+
+template <int B, int S>
+inline int64_t row_threads_s(int nbr) {
+  constexpr int RPW = 32 / (B * S);
+  return (int64_t)((nbr + RPW - 1) / RPW) * 32;
+}
+
+// Sum over the S lanes of a row; the total lands in the s == 0 lane.  All
+// 32 lanes must call it.
+template <int B, int S, class AT>
+__device__ __forceinline__ AT split_reduce(AT v) {
+#pragma unroll
+  for (int off = S / 2; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off * B);
+  return v;
+}
+
+// Row r of (A x) for block row `brow` (A x or A^T x through tmap), over
+// the blocks k0 + s, k0 + s + S, ... of the row.
+template <int B, bool TR, class VT, class XT, class AT, int S = 1>
 __device__ __forceinline__ AT row_dot(const DevBsr<VT>& A, const XT* __restrict__ x, int brow,
-                                      int r) {
+                                      int r, int s = 0) {
   AT acc = AT(0);
   const int k0 = A.rp[brow], k1 = A.rp[brow + 1];
 #pragma unroll 4
-  for (int k = k0; k < k1; ++k) {
+  for (int k = k0 + s; k < k1; k += S) {
     const int j = __ldg(A.col + k);
     AT a[B], xv[B];
     if constexpr (!TR) {
@@ -171,25 +211,30 @@ struct Geom {
 // accumulation is not ALU-bound and uses coalesced lane groups sized by
 // row length; a whole 256-thread CTA per row when there are few, very
 // long rows.
+// Row split S for one-lane-per-scalar-row levels: long rows are shared by
+// S lanes (one FP add per reduction step).
+template <int B>
+inline int choose_split(int64_t nbr, int64_t nnzb) {
+  const double avg = nbr ? (double)nnzb / nbr : 0.0;
+  int S = 1;
+  if (avg >= 12.0) S = 2;
+  if (avg >= 24.0) S = 4;
+  if (avg >= 48.0) S = 8;
+  while (S > 1 && B * S > 32) S >>= 1;
+  return S;
+}
+
 template <int B, class VT, class AT>
 inline int choose_group(int64_t nbr, int64_t nnzb) {
   using Gm = Geom<B, VT>;
   const double avg = nbr ? (double)nnzb / nbr : 0.0;
   const double chunks = avg * (Gm::FIXED ? Gm::LPB : B * B);
-  if (sizeof(AT) == 8) {
-    if (avg < 40.0) return 0;
-    if (nbr > 1024) return 32;
-    return 256;
-  }
-  if (!Gm::FIXED) {
-    // aligned-chunk streaming (two chunks per lane per batch) pays index
-    // work per value: short rows stay one lane per scalar row
-    if (avg < 40.0) return 0;
-    const double c16 = avg * Gm::BB / 16.0;
-    if (c16 <= 16) return 8;
-    if (c16 <= 32) return 16;
-    if (c16 <= 64 || nbr > 4096) return 32;
-    return 256;
+  if (sizeof(AT) == 8 || !Gm::FIXED) {
+    // FP64 (pipe-bound) and 3x3 / scalar FP32-BF16 rows: one lane per
+    // scalar row with a row split (choose_split); a CTA per row only for a
+    // few very long rows
+    if (nbr <= 1024 && avg >= 128.0) return 256;
+    return 0;
   }
   if (chunks <= 48) return 8;
   if (chunks <= 96) return 16;
@@ -405,13 +450,16 @@ __device__ __forceinline__ AT pick(const AT (&v)[B], int r) {
 // ------------------------------------------------------------------ kernels
 enum { SPMV_SET = 0, SPMV_RESID = 1, SPMV_ADD = 2 };
 
-// MODE SET: y = A x;  RESID: y = f - A x;  ADD: y += A x.
-template <int B, bool TR, int MODE, class VT, class XT, class YT, class AT>
+// MODE SET: y = A x;  RESID: y = f - A x;  ADD: y += A x.  One lane per
+// scalar row, or S lanes per scalar row (row split).
+template <int B, int S, bool TR, int MODE, class VT, class XT, class YT, class AT>
 __global__ void __launch_bounds__(256, 4) k_spmv(DevBsr<VT> A, const XT* __restrict__ x,
                                               const YT* __restrict__ f, YT* __restrict__ y) {
-  RowMap<B> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
-  if (!m.lane_ok || m.brow >= A.nbr) return;
-  AT acc = row_dot<B, TR, VT, XT, AT>(A, x, m.brow, m.r);
+  RowMapS<B, S> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  const bool ok = m.lane_ok && m.brow < A.nbr;
+  AT acc = ok ? row_dot<B, TR, VT, XT, AT, S>(A, x, m.brow, m.r, m.s) : AT(0);
+  if constexpr (S > 1) acc = split_reduce<B, S, AT>(acc);
+  if (!ok || m.s != 0) return;
   const size_t o = (size_t)m.brow * B + m.r;
   if constexpr (MODE == SPMV_SET) y[o] = (YT)acc;
   else if constexpr (MODE == SPMV_RESID) y[o] = (YT)(cvt<AT>(f[o]) - acc);
@@ -460,20 +508,22 @@ __global__ void __launch_bounds__(256, 4) k_relax_w(DevBsr<VT> A, const VT* __re
   xo[o] = (XT)out;
 }
 
-// xo = x + M (f - A x)   (one relaxation sweep; M^T, A^T when TR).
-template <int B, bool TR, class VT, class XT, class AT>
+// xo = x + M (f - A x)   (one relaxation sweep; M^T, A^T when TR).  One
+// lane per scalar row or S lanes per scalar row.
+template <int B, int S, bool TR, class VT, class XT, class AT>
 __global__ void __launch_bounds__(256, 4) k_relax(DevBsr<VT> A, const VT* __restrict__ M,
                                                const XT* __restrict__ f,
                                                const XT* __restrict__ x, XT* __restrict__ xo) {
-  RowMap<B> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  RowMapS<B, S> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   const bool ok = m.lane_ok && m.brow < A.nbr;
   const size_t o = (size_t)m.brow * B + m.r;
-  AT res = AT(0);
-  if (ok) res = cvt<AT>(f[o]) - row_dot<B, TR, VT, XT, AT>(A, x, m.brow, m.r);
+  AT acc = ok ? row_dot<B, TR, VT, XT, AT, S>(A, x, m.brow, m.r, m.s) : AT(0);
+  if constexpr (S > 1) acc = split_reduce<B, S, AT>(acc);
+  const AT res = (ok && m.s == 0) ? cvt<AT>(f[o]) - acc : AT(0);
   AT rb[B];
 #pragma unroll
   for (int c = 0; c < B; ++c) rb[c] = __shfl_sync(0xffffffffu, res, (m.base + c) & 31);
-  if (!ok) return;
+  if (!ok || m.s != 0) return;
   AT mr[B];
   if constexpr (!TR) load_run<B, VT, AT, false>(M + (size_t)m.brow * (B * B) + m.r * B, mr);
   else load_col<B, VT, AT>(M + (size_t)m.brow * (B * B), m.r, mr);

@@ -320,55 +320,6 @@ static __global__ void __launch_bounds__(RED_THREADS, 4)
   if (threadIdx.x == 0) R.counter[slot] = 0u;
 }
 
-// Single-pass multi-dot for J <= JM: every thread reads w once and keeps
-// all J partial dots (plus w.w) in registers.  Same outputs as k_multidot.
-template <int JM>
-static __global__ void __launch_bounds__(RED_THREADS, 2)
-    k_multidot1(int64_t n, const double* __restrict__ V, int J, const double* __restrict__ w,
-                double* __restrict__ h, Red R, int slot, const double* __restrict__ gate) {
-  if (gate && *gate == 0.0) return;
-  double v[JM + 1];
-#pragma unroll
-  for (int q = 0; q <= JM; ++q) v[q] = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double wi = w[i];
-#pragma unroll
-    for (int q = 0; q < JM; ++q)
-      if (q < J) v[q] += V[(size_t)q * n + i] * wi;
-    v[JM] += wi * wi;
-  }
-  __shared__ double sh[RED_THREADS / 32][JM + 1];
-  __shared__ bool last;
-  block_sum<JM + 1>(v, sh);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int q = 0; q < JM; ++q)
-      if (q < J) R.partials[(size_t)blockIdx.x * MAX_DOTS + q] = v[q];
-    R.partials[(size_t)blockIdx.x * MAX_DOTS + J] = v[JM];
-    __threadfence();
-    unsigned t = atomicAdd(R.counter + slot, 1u);
-    last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  // the last block: reduce column q of the partials in block order
-  for (int q = threadIdx.x >> 5; q <= J; q += RED_THREADS / 32) {
-    double acc = 0.0;
-    for (int b = threadIdx.x & 31; b < (int)gridDim.x; b += 32)
-      acc += __ldcg(R.partials + (size_t)b * MAX_DOTS + q);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) {
-      if (q < J) h[q] = acc;
-      else R.sc[S_WW0] = acc;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) R.counter[slot] = 0u;
-}
-
 // w -= sum_i h[i] V_i; sc[S_WW] = w.w; sc[S_REORTH] = (ww < 0.5 ww0).
 // accumulate (non-null): hacc[i] += h[i] as well (second pass).
 static __global__ void __launch_bounds__(RED_THREADS, 4)

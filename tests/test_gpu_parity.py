@@ -113,13 +113,15 @@ def test_vcycle_on_imported_oracle_hierarchy(cfg):
         assert rel_inf(z, ref) <= 1e-12, (tr, rel_inf(z, ref))
 
 
-@pytest.mark.parametrize("G", ["0", "8", "16", "32", "256"])
+@pytest.mark.parametrize("G,S", [("0", "1"), ("0", "2"), ("0", "4"), ("0", "8"), ("8", "1"),
+                                 ("16", "1"), ("32", "1"), ("256", "1")])
 @pytest.mark.parametrize("name", ["c2", "c1"])
-def test_vcycle_every_lane_group_width(name, G, monkeypatch):
-    """Force each SpMV lane-group width (one lane per scalar row, 8, 16 or
-    32 lanes, or a 256-thread CTA per block row) on every level and compare
-    with the oracle."""
+def test_vcycle_every_lane_group_width(name, G, S, monkeypatch):
+    """Force each SpMV lane mapping on every level -- one lane per scalar row
+    with a row split over S = 1, 2, 4, 8 lanes, or G = 8, 16, 32 lanes or a
+    256-thread CTA per block row -- and compare with the oracle."""
     monkeypatch.setenv("GBS_SPMV_GROUP", G)
+    monkeypatch.setenv("GBS_SPMV_SPLIT", S)
     s = si.make_system(name, N=9)
     B = s.bdim
     A = bsr.from_arrays(s.indptr, s.indices, s.data, B)
@@ -159,6 +161,24 @@ def test_schur_apply_matches_oracle():
         z = host(gb.apply_precond(H, dev(r), transpose=tr))
         ref = pc.apply(r, transpose=tr)
         assert rel_inf(z, ref) <= 1e-10, (tr, rel_inf(z, ref))
+
+
+@pytest.mark.parametrize("S", ["1", "2", "4", "8"])
+def test_schur_apply_every_row_split(S, monkeypatch):
+    """3x3 velocity and scalar pressure hierarchies with each row split."""
+    monkeypatch.setenv("GBS_SPMV_SPLIT", S)
+    s = si.make_system("c3", N=9)
+    K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    po = amg.AmgParams(coarse_enough=60)
+    pc = schur.build(K, 3, po, po)
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
+                           gb.params_default(precond=gb.GBS_PC_SCHUR, krylov=gb.GBS_GMRES,
+                                             coarse_enough=60))
+    rng = np.random.default_rng(int(S))
+    for tr in (False, True):
+        r = rng.standard_normal(K.shape[0])
+        z = host(gb.apply_precond(H, dev(r), transpose=tr))
+        assert rel_inf(z, pc.apply(r, transpose=tr)) <= 1e-10
 
 
 @pytest.mark.parametrize("precision", [gb.GBS_FP32, gb.GBS_BF16])
@@ -379,3 +399,71 @@ def test_full_size_c3_true_residual(precision):
     x = host(x)
     assert info.converged
     assert _true_rel(s, x) <= 1e-8
+
+
+def test_full_size_c4_adjoint_central_differences():
+    """C4 at full size (N=64, 4x4 BSR FP64): L = 1/2 ||x - x_t||^2, adjoint
+    gradient of 64 random stored entries (seed 4002) against FP64 central
+    differences (h = 1e-6) with solves to 1e-13 reusing the hierarchy.
+    Tolerance: 1e-5 relative per entry, with entries below 1% of max|G|
+    compared at 1e-7 max|G| (the difference quotient's noise from 1e-13
+    solves divided by the step)."""
+    from paper_2006_06052_gb300.autograd import stokes_solve
+    s = si.make_system("c4")
+    xt = dev(si.gaussian_vector(s.n, 4001))
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
+                           _params(s, relax=gb.GBS_JACOBI, tol=1e-13, maxiter=3000))
+    v0 = dev(s.data.reshape(-1))
+    vals = v0.clone().requires_grad_(True)
+    b = dev(s.b).requires_grad_(True)
+    x = stokes_solve(vals, b, H)
+    (0.5 * ((x - xt) ** 2).sum()).backward()
+    G = host(vals.grad)
+    gb_ = host(b.grad)
+    rng = np.random.Generator(np.random.PCG64(4002))
+    flat = s.data.reshape(-1)
+    nz = np.nonzero(flat)[0]
+    gmax = np.abs(G).max()
+    for idx in rng.choice(nz, size=64, replace=False):
+        step = 1e-6 * max(1.0, abs(float(flat[idx])))
+        vp, vm = v0.clone(), v0.clone()
+        vp[idx] += step
+        vm[idx] -= step
+        with torch.no_grad():
+            xp = stokes_solve(vp, dev(s.b), H)
+            xm = stokes_solve(vm, dev(s.b), H)
+        fd = 0.5 * torch.dot(xp - xm, xp + xm - 2 * xt).item() / (2 * step)
+        assert abs(fd - G[idx]) <= 1e-5 * max(abs(fd), 1e-2 * gmax), (idx, fd, G[idx])
+    # grad_b by central differences on a few unknowns
+    for i in rng.integers(s.n, size=4):
+        e = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+        e[int(i)] = 1e-6
+        with torch.no_grad():
+            xp = stokes_solve(v0, dev(s.b) + e, H)
+            xm = stokes_solve(v0, dev(s.b) - e, H)
+        fd = 0.5 * torch.dot(xp - xm, xp + xm - 2 * xt).item() / 2e-6
+        assert abs(fd - gb_[int(i)]) <= 1e-5 * max(abs(fd), 1e-2 * np.abs(gb_).max())
+
+
+@pytest.mark.parametrize("N", [24, pytest.param(128, id="full_size")])
+def test_c5_mixed_adjoint_matches_fp64_adjoint(N):
+    """C5 (full size at N=128): BF16/FP32 Schur hierarchy shared by the
+    forward and the transposed backward, only x kept (the backward recomputes
+    the adjoint solve); ||grad_b|| within 1e-5 of the FP64 GPU adjoint."""
+    from paper_2006_06052_gb300.autograd import stokes_solve
+    s = si.make_system("c5", N=N)
+    xt = dev(si.gaussian_vector(s.n, 5001))
+    grads = {}
+    for prec in (gb.GBS_BF16, gb.GBS_FP64):
+        H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, _params(s, precision=prec))
+        vals = dev(s.data.reshape(-1)).requires_grad_(True)
+        b = dev(s.b).requires_grad_(True)
+        x = stokes_solve(vals, b, H)
+        (0.5 * ((x - xt) ** 2).sum()).backward()
+        grads[prec] = (host(b.grad), vals.grad.norm().item())
+        del H
+    g16, g64 = grads[gb.GBS_BF16][0], grads[gb.GBS_FP64][0]
+    n16, n64 = np.linalg.norm(g16), np.linalg.norm(g64)
+    assert abs(n16 - n64) <= 1e-5 * n64
+    assert np.linalg.norm(g16 - g64) <= 1e-4 * n64
+    assert abs(grads[gb.GBS_BF16][1] - grads[gb.GBS_FP64][1]) <= 1e-4 * grads[gb.GBS_FP64][1]
