@@ -418,7 +418,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         vms = e0.elapsed_time(e1) / 20
-        vb = vcycle_bytes(gb, H, B, spec["precision"])
+        vb = gb.precond_bytes(H)
         vcycle = {"ms": vms, "algorithmic_bytes": vb, "achieved_gbs": vb / (vms * 1e-3) / 1e9,
                   "frac": vb / (vms * 1e-3) / 1e9 / peak}
 

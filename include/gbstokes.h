@@ -98,6 +98,10 @@ typedef struct {
   int32_t enable_adjoint; /* 1: build transpose maps for solve_adjoint */
   int32_t setup_only;     /* 1: build the host hierarchy only (no device work,
                              no GPU needed); export/info work, solves do not */
+  int32_t level_format;   /* 0: hierarchy levels whose stored blocks are at most
+                             half nonzero run as scalar CSR of their nonzeros
+                             (same operator, fewer bytes and FMAs); 1: keep
+                             every level in block form */
 } gbs_params;
 
 typedef struct {
@@ -175,6 +179,11 @@ gbs_status gbs_apply_precond(gbs_hierarchy* h, const double* r_dev, double* z_de
 gbs_status gbs_hierarchy_info(const gbs_hierarchy* h, int32_t which, int32_t* nlevels,
                               int32_t* n_brows, int64_t* nnzb, int32_t cap,
                               int64_t* bytes);
+
+/* Algorithmic bytes that one preconditioner application moves (values,
+ * indices and vectors of every kernel it launches, from the formats the
+ * hierarchy is stored in).  Used for bandwidth reporting. */
+gbs_status gbs_precond_bytes(const gbs_hierarchy* h, double* bytes_per_apply);
 
 /* Copy level l (0 = finest) of AMG `which` to host arrays.  part: 0 = A,
  * 1 = P, 2 = R, 3 = smoother blocks M (row_ptr/col_idx untouched),

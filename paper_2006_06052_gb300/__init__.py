@@ -20,7 +20,7 @@ from ._build import LIB as _LIB_PATH, build as _build_lib
 __all__ = [
     "GbsError", "Params", "Info", "Hierarchy", "params_default", "build_hierarchy",
     "import_hierarchy", "solve", "solve_adjoint", "sampled_outer", "update_values", "spmv",
-    "apply_precond", "hierarchy_info", "export_level", "export_level_sizes", "spmv_dots_noalloc", "load_library", "build", "kernel_launches",
+    "apply_precond", "hierarchy_info", "export_level", "export_level_sizes", "spmv_dots_noalloc", "precond_bytes", "load_library", "build", "kernel_launches",
     "GBS_PC_AMG", "GBS_PC_SCHUR", "GBS_BICGSTAB", "GBS_GMRES", "GBS_FP64", "GBS_FP32",
     "GBS_BF16", "GBS_SPAI0", "GBS_JACOBI", "EXPORTED",
 ]
@@ -39,7 +39,7 @@ EXPORTED = [
     "gbs_params_default", "gbs_build_hierarchy", "gbs_solve", "gbs_solve_adjoint",
     "gbs_sampled_outer", "gbs_update_values", "gbs_spmv", "gbs_apply_precond",
     "gbs_hierarchy_info", "gbs_export_level", "gbs_import_hierarchy", "gbs_destroy",
-    "gbs_last_error", "gbs_kernel_launches", "gbs_spmv_dots_noalloc",
+    "gbs_last_error", "gbs_kernel_launches", "gbs_spmv_dots_noalloc", "gbs_precond_bytes",
 ]
 
 
@@ -59,7 +59,7 @@ class Params(ctypes.Structure):
         ("relax_p", ctypes.c_int32), ("jacobi_omega", ctypes.c_double),
         ("smooth_P", ctypes.c_int32), ("power_iters", ctypes.c_int32), ("nvel", ctypes.c_int32),
         ("use_graph", ctypes.c_int32), ("enable_adjoint", ctypes.c_int32),
-        ("setup_only", ctypes.c_int32),
+        ("setup_only", ctypes.c_int32), ("level_format", ctypes.c_int32),
     ]
 
 
@@ -121,6 +121,7 @@ def load_library():
         "gbs_import_hierarchy": [c.POINTER(_Bsr), c.POINTER(_Bsr), c.POINTER(_Bsr),
                                  c.POINTER(P), P, c.c_int32, c.POINTER(Params), P, c.POINTER(P)],
         "gbs_destroy": [P],
+        "gbs_precond_bytes": [P, c.POINTER(c.c_double)],
         "gbs_spmv_dots_noalloc": [c.c_int32, c.c_int32, c.c_int32, c.c_int64, P, P, P, P, P, P,
                                   P, P],
     }
@@ -348,6 +349,13 @@ def hierarchy_info(H: Hierarchy, which: int = 0):
                                   ctypes.byref(by)))
     k = nl.value
     return dict(nlevels=k, n_brows=list(rows[:k]), nnzb=list(nnz[:k]), bytes=by.value)
+
+
+def precond_bytes(H: Hierarchy) -> float:
+    """Algorithmic bytes of one preconditioner application (stored formats)."""
+    v = ctypes.c_double()
+    _check(load_library().gbs_precond_bytes(H.handle, ctypes.byref(v)))
+    return v.value
 
 
 def export_level_sizes(H: Hierarchy, which: int, level: int, part: int):

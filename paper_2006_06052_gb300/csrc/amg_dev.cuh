@@ -102,6 +102,71 @@ DevBsr<VT> upload_bsr(Arena& ar, const HBsr& H, bool with_tmap, cudaStream_t s,
   return d;
 }
 
+template <class VT>
+DevCsr<VT> upload_csr(Arena& ar, const HCsr& C, cudaStream_t s, std::vector<std::vector<VT>>& keep) {
+  DevCsr<VT> d;
+  d.n = C.n;
+  d.rp = ar.upload(C.ptr.data(), C.ptr.size(), s);
+  d.col = ar.upload(C.col.data(), C.col.size(), s);
+  keep.push_back(cast_vec<VT>(C.val));
+  d.val = ar.upload(keep.back().data(), keep.back().size(), s);
+  d.S = csr_split(C.n, (int64_t)C.col.size());
+  if (const char* e = std::getenv("GBS_SPMV_SPLIT")) {
+    int sp = std::atoi(e);
+    if (sp == 1 || sp == 2 || sp == 4 || sp == 8) d.S = sp;
+  }
+  return d;
+}
+
+// Per-level format choice: a level whose stored blocks are at most half
+// nonzero is kept as scalar CSR of its nonzeros (fewer bytes and, on the
+// FP64 pipe, fewer FMAs); dense-block levels stay block CSR.
+inline bool use_scalar_csr(const HBsr& H, int level_format) {
+  int f = level_format;
+  if (const char* e = std::getenv("GBS_LEVEL_FORMAT")) f = std::atoi(e);
+  if (f == 1 || H.br * H.bc == 1) return false;
+  if (f == 2) return true;   // test override: CSR wherever possible
+  return block_fill(H) <= 0.5;
+}
+
+template <int MODE, class VT, class XT, class YT, class AT>
+void csr_spmv(const DevCsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
+  if (A.n == 0) return;
+  switch (A.S) {
+    case 2: k_csr_spmv<2, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<1, 2>(A.n)), 256, 0, s>>>(A, x, f, y); break;
+    case 4: k_csr_spmv<4, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<1, 4>(A.n)), 256, 0, s>>>(A, x, f, y); break;
+    case 8: k_csr_spmv<8, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<1, 8>(A.n)), 256, 0, s>>>(A, x, f, y); break;
+    default: k_csr_spmv<1, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<1, 1>(A.n)), 256, 0, s>>>(A, x, f, y);
+  }
+  GBS_LAUNCH_CHECK();
+}
+template <int B, class VT, class XT, class AT>
+void csr_relax_B(const DevCsr<VT>& A, const VT* M, const XT* f, const XT* x, XT* xo, cudaStream_t s) {
+  const int nn = A.n / B;
+  switch (A.S) {
+    case 2: k_csr_relax<B, 2, VT, XT, AT><<<grid_for(row_threads_s<B, 2>(nn)), 256, 0, s>>>(A, M, f, x, xo); break;
+    case 4:
+      if constexpr (B * 4 <= 32) k_csr_relax<B, 4, VT, XT, AT><<<grid_for(row_threads_s<B, 4>(nn)), 256, 0, s>>>(A, M, f, x, xo);
+      break;
+    case 8:
+      if constexpr (B * 8 <= 32) k_csr_relax<B, 8, VT, XT, AT><<<grid_for(row_threads_s<B, 8>(nn)), 256, 0, s>>>(A, M, f, x, xo);
+      break;
+    default: k_csr_relax<B, 1, VT, XT, AT><<<grid_for(row_threads_s<B, 1>(nn)), 256, 0, s>>>(A, M, f, x, xo);
+  }
+}
+template <class VT, class XT, class AT>
+void csr_relax(int B, DevCsr<VT> A, const VT* M, const XT* f, const XT* x, XT* xo, cudaStream_t s) {
+  if (A.n == 0) return;
+  while (A.S > 1 && B * A.S > 32) A.S >>= 1;
+  switch (B) {
+    case 1: csr_relax_B<1, VT, XT, AT>(A, M, f, x, xo, s); break;
+    case 2: csr_relax_B<2, VT, XT, AT>(A, M, f, x, xo, s); break;
+    case 3: csr_relax_B<3, VT, XT, AT>(A, M, f, x, xo, s); break;
+    case 4: csr_relax_B<4, VT, XT, AT>(A, M, f, x, xo, s); break;
+  }
+  GBS_LAUNCH_CHECK();
+}
+
 // ------------------------------------------------------------ launch helpers
 template <int B, bool TR, int MODE, class VT, class XT, class YT, class AT>
 void spmv_B(const DevBsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
@@ -198,10 +263,13 @@ struct DevAmg {
 
   struct Lev {
     DevBsr<VT> A, Pm, R;
+    DevCsr<VT> Ac, Pc, Rc;              // scalar CSR forms (per-level format choice)
+    bool a_csr = false, p_csr = false, r_csr = false;
     const VT* M = nullptr;
     ST *f = nullptr, *r = nullptr, *x = nullptr, *xt = nullptr, *e = nullptr;
     int64_t n = 0;
     int64_t nnzb_A = 0, nnzb_P = 0, nnzb_R = 0;
+    int64_t nnz_A = 0, nnz_P = 0, nnz_R = 0;  // scalar nonzeros when in CSR
   };
   int B = 1;
   int npre = 1, npost = 1;
@@ -220,9 +288,31 @@ struct DevAmg {
       const HLevel& h = H.levels[l];
       Lev L;
       L.n = (int64_t)h.A.nbr * B;
-      L.A = upload_bsr<VT, AT>(ar, h.A, o.tmaps, s, keep);
-      L.Pm = upload_bsr<VT, AT>(ar, h.P, false, s, keep);
-      L.R = upload_bsr<VT, AT>(ar, h.R, false, s, keep);
+      L.a_csr = use_scalar_csr(h.A, o.level_format);
+      L.p_csr = use_scalar_csr(h.P, o.level_format);
+      L.r_csr = use_scalar_csr(h.R, o.level_format);
+      // the block form of A stays resident when the adjoint may need A^T
+      if (!L.a_csr || o.tmaps) L.A = upload_bsr<VT, AT>(ar, h.A, o.tmaps, s, keep);
+      else { L.A.nbr = h.A.nbr; L.A.nbc = h.A.nbc; }
+      if (L.a_csr) {
+        HCsr c = to_scalar_csr(h.A);
+        L.nnz_A = (int64_t)c.col.size();
+        L.Ac = upload_csr<VT>(ar, c, s, keep);
+      }
+      if (L.p_csr) {
+        HCsr c = to_scalar_csr(h.P);
+        L.nnz_P = (int64_t)c.col.size();
+        L.Pc = upload_csr<VT>(ar, c, s, keep);
+      } else {
+        L.Pm = upload_bsr<VT, AT>(ar, h.P, false, s, keep);
+      }
+      if (L.r_csr) {
+        HCsr c = to_scalar_csr(h.R);
+        L.nnz_R = (int64_t)c.col.size();
+        L.Rc = upload_csr<VT>(ar, c, s, keep);
+      } else {
+        L.R = upload_bsr<VT, AT>(ar, h.R, false, s, keep);
+      }
       keep.push_back(cast_vec<VT>(h.M));
       L.M = ar.upload(keep.back().data(), keep.back().size(), s);
       L.f = ar.alloc<ST>(L.n);
@@ -271,23 +361,31 @@ struct DevAmg {
     const int post = TR ? npre : npost;
     ST* x = L.x;
     ST* xt = L.xt;
+    const bool acsr = L.a_csr && !TR;   // A^T goes through the block form's transpose map
+    auto sweep = [&](const ST* xin, ST* xout) {
+      if (acsr) csr_relax<VT, ST, AT>(B, L.Ac, L.M, f, xin, xout, s);
+      else relax<TR, VT, ST, AT>(B, L.A, L.M, f, xin, xout, s);
+    };
     if (pre >= 1) {
       mapply<TR, VT, ST, AT>(B, nb, L.M, f, x, s);
       for (int it = 1; it < pre; ++it) {
-        relax<TR, VT, ST, AT>(B, L.A, L.M, f, x, xt, s);
+        sweep(x, xt);
         std::swap(x, xt);
       }
     } else {
       GBS_CUDA(cudaMemsetAsync(x, 0, sizeof(ST) * L.n, s));
     }
-    spmv<TR, SPMV_RESID, VT, ST, ST, AT>(B, L.A, x, f, L.r, s);
+    if (acsr) csr_spmv<SPMV_RESID, VT, ST, ST, AT>(L.Ac, x, f, L.r, s);
+    else spmv<TR, SPMV_RESID, VT, ST, ST, AT>(B, L.A, x, f, L.r, s);
     Lev& Cn = lev[l + 1];
-    spmv<false, SPMV_SET, VT, ST, ST, AT>(B, L.R, L.r, (const ST*)nullptr, Cn.f, s);
+    if (L.r_csr) csr_spmv<SPMV_SET, VT, ST, ST, AT>(L.Rc, L.r, (const ST*)nullptr, Cn.f, s);
+    else spmv<false, SPMV_SET, VT, ST, ST, AT>(B, L.R, L.r, (const ST*)nullptr, Cn.f, s);
     cycle<TR>(l + 1, Cn.f, Cn.e, s);
-    spmv<false, SPMV_ADD, VT, ST, ST, AT>(B, L.Pm, Cn.e, (const ST*)nullptr, x, s);
+    if (L.p_csr) csr_spmv<SPMV_ADD, VT, ST, ST, AT>(L.Pc, Cn.e, (const ST*)nullptr, x, s);
+    else spmv<false, SPMV_ADD, VT, ST, ST, AT>(B, L.Pm, Cn.e, (const ST*)nullptr, x, s);
     for (int it = 0; it < post; ++it) {
       ST* dst = (it + 1 == post) ? out : xt;
-      relax<TR, VT, ST, AT>(B, L.A, L.M, f, x, dst, s);
+      sweep(x, dst);
       std::swap(x, xt);
     }
   }
@@ -303,9 +401,13 @@ struct DevAmg {
     for (size_t l = 0; l + 1 < lev.size(); ++l) {
       const Lev& L = lev[l];
       const double nb = (double)L.A.nbr;
-      const double Abytes = L.nnzb_A * (B * B * sv + 4) + 4 * (nb + 1);
-      const double Pbytes = L.nnzb_P * (B * B * sv + 4) + 4 * (nb + 1);
-      const double Rbytes = L.nnzb_R * (B * B * sv + 4) + 4 * (L.R.nbr + 1);
+      const double nc = (double)(lev[l + 1].n / B);
+      const double Abytes = L.a_csr ? L.nnz_A * (sv + 4) + 4 * (L.n + 1.0)
+                                    : L.nnzb_A * (B * B * sv + 4) + 4 * (nb + 1);
+      const double Pbytes = L.p_csr ? L.nnz_P * (sv + 4) + 4 * (L.n + 1.0)
+                                    : L.nnzb_P * (B * B * sv + 4) + 4 * (nb + 1);
+      const double Rbytes = L.r_csr ? L.nnz_R * (sv + 4) + 4 * (nc * B + 1)
+                                    : L.nnzb_R * (B * B * sv + 4) + 4 * (nc + 1);
       const double Mbytes = nb * B * B * sv;
       // mapply (M, f, x) + resid (A, x, f, r) + restrict (R, r, fc)
       // + prolong (P, ec, x rw) + relax (A, M, f, x, out)

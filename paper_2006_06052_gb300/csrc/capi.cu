@@ -105,6 +105,7 @@ void check_params(const gbs_params* p) {
   if (p->max_levels < 1 || p->coarse_enough < 1) throw SetupError{"bad level limits"};
   if (p->precond == GBS_PC_SCHUR && (p->nvel < 1 || p->nvel > 3))
     throw SetupError{"nvel must be in 1..3"};
+  if (p->level_format < 0 || p->level_format > 1) throw SetupError{"level_format must be 0 or 1"};
 }
 
 AmgSetupParams amg_prm(const gbs_params* p, int relax) {
@@ -125,6 +126,7 @@ PrecondOptions pc_opts(const gbs_params* p) {
   o.npre = p->npre;
   o.npost = p->npost;
   o.tmaps = p->enable_adjoint != 0;
+  o.level_format = p->level_format;
   return o;
 }
 
@@ -598,6 +600,7 @@ gbs_status gbs_params_default(gbs_params* p) {
   p->use_graph = 1;
   p->enable_adjoint = 1;
   p->setup_only = 0;
+  p->level_format = 0;
   return GBS_OK;
 }
 
@@ -778,6 +781,15 @@ gbs_status gbs_hierarchy_info(const gbs_hierarchy* hh, int32_t which, int32_t* n
       if (nnzb) nnzb[l] = A.nnzb();
     }
     if (bytes) *bytes = h.pc ? h.pc->bytes() + h.ar.bytes : 0;
+    return GBS_OK;
+  });
+}
+
+gbs_status gbs_precond_bytes(const gbs_hierarchy* hh, double* bytes) {
+  return guarded([&]() -> gbs_status {
+    if (!hh || !bytes) throw SetupError{"null argument"};
+    need_device(hh->h);
+    *bytes = hh->h.pc->bytes_per_apply();
     return GBS_OK;
   });
 }

@@ -81,6 +81,7 @@ struct PrecondOptions {
   int precision = 0;   // 0 FP64, 1 FP32, 2 BF16
   int npre = 1, npost = 1;
   bool tmaps = true;
+  int level_format = 0;  // 0: scalar CSR for levels whose blocks are mostly zeros; 1: always blocks
 };
 
 std::unique_ptr<DevPrecond> make_amg_precond(const HAmg& H, const PrecondOptions& o,

@@ -35,6 +35,25 @@ struct DevBsr {
 };
 
 
+// Scalar CSR of a level whose blocks are mostly zeros (per-level format
+// choice): n scalar rows, S lanes per scalar row.
+template <class VT>
+struct DevCsr {
+  int n = 0;
+  const int* rp = nullptr;
+  const int* col = nullptr;
+  const VT* val = nullptr;
+  int S = 1;
+};
+
+inline int csr_split(int64_t n, int64_t nnz) {
+  const double avg = n ? (double)nnz / n : 0.0;
+  if (avg < 12.0) return 1;
+  if (avg < 24.0) return 2;
+  if (avg < 48.0) return 4;
+  return 8;
+}
+
 // ---------------------------------------------------------------- conversions
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(double v) { return (float)v; }
@@ -531,6 +550,59 @@ __global__ void __launch_bounds__(256, 4) k_relax(DevBsr<VT> A, const VT* __rest
 #pragma unroll
   for (int c = 0; c < B; ++c) out += mr[c] * rb[c];
   xo[o] = (XT)out;
+}
+
+// ------------------------------------------------------- scalar CSR levels
+template <int S, class VT, class XT, class AT>
+__device__ __forceinline__ AT csr_row_dot(const DevCsr<VT>& A, const XT* __restrict__ x, int row,
+                                          int s) {
+  AT acc = AT(0);
+  const int k0 = A.rp[row], k1 = A.rp[row + 1];
+#pragma unroll 4
+  for (int k = k0 + s; k < k1; k += S)
+    acc += cvt<AT>(__ldcs(A.val + k)) * cvt<AT>(__ldg(x + __ldg(A.col + k)));
+  return acc;
+}
+
+// MODE SET / RESID / ADD on a scalar CSR level; S lanes per scalar row.
+template <int S, int MODE, class VT, class XT, class YT, class AT>
+__global__ void __launch_bounds__(256, 4) k_csr_spmv(DevCsr<VT> A, const XT* __restrict__ x,
+                                                  const YT* __restrict__ f, YT* __restrict__ y) {
+  RowMapS<1, S> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  const bool ok = m.lane_ok && m.brow < A.n;
+  AT acc = ok ? csr_row_dot<S, VT, XT, AT>(A, x, m.brow, m.s) : AT(0);
+  if constexpr (S > 1) acc = split_reduce<1, S, AT>(acc);
+  if (!ok || m.s != 0) return;
+  const size_t o = (size_t)m.brow;
+  if constexpr (MODE == SPMV_SET) y[o] = (YT)acc;
+  else if constexpr (MODE == SPMV_RESID) y[o] = (YT)(cvt<AT>(f[o]) - acc);
+  else y[o] = (YT)(cvt<AT>(y[o]) + acc);
+}
+
+// xo = x + M (f - A x) with A in scalar CSR and M in B x B blocks: the B
+// scalar rows of a node (each over S lanes) meet by shuffles for M.
+template <int B, int S, class VT, class XT, class AT>
+__global__ void __launch_bounds__(256, 4) k_csr_relax(DevCsr<VT> A, const VT* __restrict__ M,
+                                                   const XT* __restrict__ f,
+                                                   const XT* __restrict__ x,
+                                                   XT* __restrict__ xo) {
+  RowMapS<B, S> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  const int nnodes = A.n / B;
+  const bool ok = m.lane_ok && m.brow < nnodes;
+  const int row = m.brow * B + m.r;
+  AT acc = ok ? csr_row_dot<S, VT, XT, AT>(A, x, row, m.s) : AT(0);
+  if constexpr (S > 1) acc = split_reduce<B, S, AT>(acc);
+  const AT res = (ok && m.s == 0) ? cvt<AT>(f[row]) - acc : AT(0);
+  AT rb[B];
+#pragma unroll
+  for (int c = 0; c < B; ++c) rb[c] = __shfl_sync(0xffffffffu, res, (m.base + c) & 31);
+  if (!ok || m.s != 0) return;
+  AT mr[B];
+  load_run<B, VT, AT, false>(M + (size_t)m.brow * (B * B) + m.r * B, mr);
+  AT out = cvt<AT>(x[row]);
+#pragma unroll
+  for (int c = 0; c < B; ++c) out += mr[c] * rb[c];
+  xo[row] = (XT)out;
 }
 
 // x = M f   (zero-guess smoothing step).

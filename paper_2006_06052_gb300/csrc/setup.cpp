@@ -510,6 +510,34 @@ HSchur schur_split(const HBsr& K, int nvel) {
   return S;
 }
 
+HCsr to_scalar_csr(const HBsr& A) {
+  HCsr C;
+  C.n = A.nbr * A.br;
+  C.ncols = A.nbc * A.bc;
+  C.ptr.assign(C.n + 1, 0);
+  const int bs = A.bsz();
+  for (int i = 0; i < A.nbr; ++i)
+    for (int a = 0; a < A.br; ++a) {
+      const int row = i * A.br + a;
+      for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
+        for (int c = 0; c < A.bc; ++c) {
+          const double v = A.val[(size_t)k * bs + a * A.bc + c];
+          if (v == 0.0) continue;
+          C.col.push_back(A.col[k] * A.bc + c);
+          C.val.push_back(v);
+        }
+      C.ptr[row + 1] = (int32_t)C.col.size();
+    }
+  return C;
+}
+
+double block_fill(const HBsr& A) {
+  if (A.val.empty()) return 1.0;
+  size_t nz = 0;
+  for (double v : A.val) nz += v != 0.0;
+  return (double)nz / (double)A.val.size();
+}
+
 bool transpose_map(const HBsr& A, std::vector<int32_t>& tmap) {
   tmap.assign(A.nnzb(), -1);
   for (int i = 0; i < A.nbr; ++i)

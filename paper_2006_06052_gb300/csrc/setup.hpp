@@ -61,6 +61,16 @@ std::vector<int32_t> aggregate(const HBsr& A, double eps, int* n_agg);
 std::vector<double> spai0(const HBsr& A);
 std::vector<double> jacobi(const HBsr& A, double omega);
 
+// Scalar CSR of the nonzero entries of a block matrix (columns sorted per
+// row); fill = nonzeros / stored block values.
+struct HCsr {
+  int n = 0, ncols = 0;
+  std::vector<int32_t> ptr, col;
+  std::vector<double> val;
+};
+HCsr to_scalar_csr(const HBsr& A);
+double block_fill(const HBsr& A);
+
 // Schur split of node blocks (nvel+1)^2 into A (nvel^2), G (nvel x 1),
 // D (1 x nvel), C (1x1) on K's block pattern, and S_hat of Eq. SchurApprox.
 struct HSchur {

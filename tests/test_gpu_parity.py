@@ -96,8 +96,12 @@ def _import(Ho, B, **kw):
     return gb.import_hierarchy(As, Ps, Rs, Ms, Ho.Ainv_coarse, B, gb.params_default(**kw))
 
 
+@pytest.mark.parametrize("fmt", ["0", "1", "2"])
 @pytest.mark.parametrize("cfg", [("c2", 9, "jacobi"), ("c2", 10, "spai0"), ("c1", 9, "spai0")])
-def test_vcycle_on_imported_oracle_hierarchy(cfg):
+def test_vcycle_on_imported_oracle_hierarchy(cfg, fmt, monkeypatch):
+    """Level formats: 0 automatic (scalar CSR where blocks are mostly zero),
+    1 block CSR everywhere, 2 scalar CSR wherever possible."""
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
     name, N, relax = cfg
     s = si.make_system(name, N=N)
     B = s.bdim
@@ -163,10 +167,13 @@ def test_schur_apply_matches_oracle():
         assert rel_inf(z, ref) <= 1e-10, (tr, rel_inf(z, ref))
 
 
+@pytest.mark.parametrize("fmt", ["1", "2"])
 @pytest.mark.parametrize("S", ["1", "2", "4", "8"])
-def test_schur_apply_every_row_split(S, monkeypatch):
-    """3x3 velocity and scalar pressure hierarchies with each row split."""
+def test_schur_apply_every_row_split(S, fmt, monkeypatch):
+    """3x3 velocity and scalar pressure hierarchies with each row split, in
+    block form and in scalar CSR form."""
     monkeypatch.setenv("GBS_SPMV_SPLIT", S)
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
     s = si.make_system("c3", N=9)
     K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
     po = amg.AmgParams(coarse_enough=60)
@@ -179,6 +186,24 @@ def test_schur_apply_every_row_split(S, monkeypatch):
         r = rng.standard_normal(K.shape[0])
         z = host(gb.apply_precond(H, dev(r), transpose=tr))
         assert rel_inf(z, pc.apply(r, transpose=tr)) <= 1e-10
+
+
+@pytest.mark.parametrize("S", ["1", "4"])
+@pytest.mark.parametrize("precision", [gb.GBS_FP32, gb.GBS_BF16])
+def test_mixed_csr_levels_match_block_levels(precision, S, monkeypatch):
+    """The scalar CSR form of a mixed-precision level computes the same
+    operator as its block form (FP32 accumulation: 1e-5 relative)."""
+    monkeypatch.setenv("GBS_SPMV_SPLIT", S)
+    s = si.make_system("c3", N=10)
+    p = _params(s, precision=precision, coarse_enough=60)
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", "1")
+    Hb = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, p)
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", "2")
+    Hc = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, p)
+    r = dev(np.random.default_rng(9).standard_normal(s.n))
+    zb = host(gb.apply_precond(Hb, r))
+    zc = host(gb.apply_precond(Hc, r))
+    assert rel_inf(zc, zb) <= 1e-5
 
 
 @pytest.mark.parametrize("precision", [gb.GBS_FP32, gb.GBS_BF16])
