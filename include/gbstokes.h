@@ -158,11 +158,15 @@ gbs_status gbs_sampled_outer(const gbs_hierarchy* h, const double* lam_dev,
                              void* stream);
 
 /* Replace the values of K (same pattern, device FP64[nnzb*bdim^2]); the
- * preconditioner is kept as built.  Asynchronous on stream. */
+ * preconditioner is kept as built.  Asynchronous on stream.  When K runs
+ * as scalar CSR of its build-time nonzeros (level_format 0), the next
+ * solve or spmv reads one device flag and switches K to its block form if
+ * a new value outside that pattern is nonzero. */
 gbs_status gbs_update_values(gbs_hierarchy* h, const double* vals_dev, void* stream);
 
 /* y = K x (transpose != 0: y = K^T x) with the library's FP64 outer SpMV.
- * x_dev, y_dev: device FP64[n].  Asynchronous on stream. */
+ * x_dev, y_dev: device FP64[n].  Asynchronous on stream (synchronises
+ * once after a gbs_update_values, see there). */
 gbs_status gbs_spmv(const gbs_hierarchy* h, const double* x_dev, double* y_dev,
                     int32_t transpose, void* stream);
 

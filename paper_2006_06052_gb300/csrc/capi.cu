@@ -36,6 +36,16 @@ struct Handle {
   HBsr Kh;                       // host copy of K (pattern + FP64 values)
   DevBsr<double> K;
   double* Kval = nullptr;
+  // K as scalar CSR of its build-time nonzeros (per-level format choice);
+  // the block form stays the source of truth for updates and K^T
+  DevCsr<double> Kc;
+  bool k_csr = false;
+  bool k_check_pending = false;
+  int* kmap = nullptr;          // CSR entry -> flat block-value index
+  int64_t kmap_n = 0;
+  double* kcval = nullptr;
+  unsigned* kzero = nullptr;    // bit i: block value i is outside the CSR pattern
+  int* kflag = nullptr;
   std::unique_ptr<DevPrecond> pc;
   bool schur = false;
   HAmg H, HA, HS;                // host hierarchies (export)
@@ -151,6 +161,33 @@ void alloc_work(Handle& h, cudaStream_t s) {
     if (g == 0 || g == 8 || g == 16 || g == 32) h.K.G = g;
     if (h.K.G == 256) h.K.G = 32;
   }
+  if (use_scalar_csr(h.Kh, h.prm.level_format)) {
+    HCsr c = to_scalar_csr(h.Kh);
+    std::vector<int32_t> map;
+    std::vector<unsigned> zero((h.Kh.val.size() + 31) / 32, 0u);
+    const int bs = h.Kh.bsz();
+    map.reserve(c.col.size());
+    for (int i = 0; i < h.Kh.nbr; ++i)
+      for (int a = 0; a < h.Kh.br; ++a)
+        for (int k = h.Kh.ptr[i]; k < h.Kh.ptr[i + 1]; ++k)
+          for (int cc = 0; cc < h.Kh.bc; ++cc) {
+            const size_t flat = (size_t)k * bs + a * h.Kh.bc + cc;
+            if (h.Kh.val[flat] != 0.0) map.push_back((int32_t)flat);
+            else zero[flat >> 5] |= 1u << (flat & 31);
+          }
+    h.Kc.n = c.n;
+    h.Kc.rp = a.upload(c.ptr.data(), c.ptr.size(), s);
+    h.Kc.col = a.upload(c.col.data(), c.col.size(), s);
+    h.kcval = a.upload(c.val.data(), c.val.size(), s);
+    h.Kc.val = h.kcval;
+    h.Kc.S = csr_split(c.n, (int64_t)c.col.size());
+    h.kmap = a.upload(map.data(), map.size(), s);
+    h.kmap_n = (int64_t)map.size();
+    h.kzero = a.upload(zero.data(), zero.size(), s);
+    h.kflag = a.alloc<int>(1);
+    GBS_CUDA(cudaMemsetAsync(h.kflag, 0, sizeof(int), s));
+    h.k_csr = true;
+  }
   if (h.prm.enable_adjoint) {
     std::vector<int32_t> tm;
     if (!transpose_map(h.Kh, tm))
@@ -211,8 +248,26 @@ void outer_B(const Handle& h, const double* x, const double* f, double* y, const
   GBS_LAUNCH_CHECK();
 }
 // y = K x or f - K x (K^T when tr); d0 = y . w0 (w0 != y), d1 = y . y if self_dot.
+template <int MODE>
+void outer_csr(const Handle& h, const double* x, const double* f, double* y, const double* w0,
+               int self_dot, int slot, int op, bool reduce, cudaStream_t s) {
+  const Red& R = h.red;
+  switch (h.Kc.S) {
+    case 2: k_outer_csr<2, MODE><<<RED_BLOCKS, RED_THREADS, 0, s>>>(h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
+    case 4: k_outer_csr<4, MODE><<<RED_BLOCKS, RED_THREADS, 0, s>>>(h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
+    case 8: k_outer_csr<8, MODE><<<RED_BLOCKS, RED_THREADS, 0, s>>>(h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
+    default: k_outer_csr<1, MODE><<<RED_BLOCKS, RED_THREADS, 0, s>>>(h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce);
+  }
+  GBS_LAUNCH_CHECK();
+}
+
 void outer(const Handle& h, bool tr, int mode, const double* x, const double* f, double* y,
            const double* w0, int self_dot, int slot, int op, bool reduce, cudaStream_t s) {
+  if (!tr && h.k_csr) {
+    if (mode == SPMV_RESID) outer_csr<SPMV_RESID>(h, x, f, y, w0, self_dot, slot, op, reduce, s);
+    else outer_csr<SPMV_SET>(h, x, f, y, w0, self_dot, slot, op, reduce, s);
+    return;
+  }
   if (tr) {
     if (mode == SPMV_RESID) outer_B<true, SPMV_RESID>(h, x, f, y, w0, self_dot, slot, op, reduce, s);
     else outer_B<true, SPMV_SET>(h, x, f, y, w0, self_dot, slot, op, reduce, s);
@@ -496,8 +551,20 @@ void need_device(const Handle& h) {
   if (!h.pc) throw SetupError{"hierarchy was built with setup_only (no device data)"};
 }
 
+// After gbs_update_values: if a new nonzero fell outside K's CSR pattern,
+// K runs in block form from now on.  Reads one device flag (synchronises s).
+void settle_k_format(Handle& h, cudaStream_t s) {
+  if (!h.k_csr || !h.k_check_pending) return;
+  int flag = 0;
+  GBS_CUDA(cudaMemcpyAsync(&flag, h.kflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GBS_CUDA(cudaStreamSynchronize(s));
+  h.k_check_pending = false;
+  if (flag) h.k_csr = false;
+}
+
 gbs_status solve(Handle& h, const double* b, double* x, bool tr, cudaStream_t s, gbs_info* info) {
   need_device(h);
+  settle_k_format(h, s);
   if (!b || !x) throw SetupError{"null vector"};
   need_aligned(b, "b");
   need_aligned(x, "x");
@@ -730,8 +797,17 @@ gbs_status gbs_update_values(gbs_hierarchy* hh, const double* vals, void* stream
     Handle& h = hh->h;
     need_device(h);
     need_aligned(vals, "vals");
+    cudaStream_t s = S(stream);
     GBS_CUDA(cudaMemcpyAsync(h.Kval, vals, sizeof(double) * h.Kh.val.size(),
-                             cudaMemcpyDeviceToDevice, S(stream)));
+                             cudaMemcpyDeviceToDevice, s));
+    if (h.k_csr) {
+      k_gather_vals<<<vgrid((int64_t)h.Kh.val.size()), 256, 0, s>>>(h.kmap_n, h.kmap, h.Kval, h.kcval);
+      GBS_LAUNCH_CHECK();
+      k_check_outside<<<vgrid((int64_t)h.Kh.val.size()), 256, 0, s>>>((int64_t)h.Kh.val.size(), h.kzero,
+                                                                      h.Kval, h.kflag);
+      GBS_LAUNCH_CHECK();
+      h.k_check_pending = true;
+    }
     return GBS_OK;
   });
 }
@@ -740,8 +816,9 @@ gbs_status gbs_spmv(const gbs_hierarchy* hh, const double* x, double* y, int32_t
                     void* stream) {
   return guarded([&]() -> gbs_status {
     if (!hh || !x || !y) throw SetupError{"null argument"};
-    const Handle& h = hh->h;
+    Handle& h = const_cast<gbs_hierarchy*>(hh)->h;
     need_device(h);
+    settle_k_format(h, S(stream));
     need_aligned(x, "x");
     need_aligned(y, "y");
     if (transpose && !h.K.tmap) throw SetupError{"built without enable_adjoint"};

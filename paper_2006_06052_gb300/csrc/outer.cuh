@@ -198,6 +198,50 @@ __global__ void __launch_bounds__(RED_THREADS, 4)
   if (reduce) grid_reduce<2>(d, R, slot, op);
 }
 
+// Outer SpMV of K held as scalar CSR (S lanes per scalar row), same
+// outputs and dots as k_outer_n; grid-stride with a warp-uniform bound.
+template <int S, int MODE>
+__global__ void __launch_bounds__(RED_THREADS, 4)
+    k_outer_csr(DevCsr<double> K, const double* __restrict__ x, const double* __restrict__ f,
+                double* __restrict__ y, const double* __restrict__ w0, int self_dot, Red R,
+                int slot, int op, int reduce) {
+  constexpr int RPW = 32 / S;
+  double d[2] = {0.0, 0.0};
+  const int64_t nwarps = ((int64_t)K.n + RPW - 1) / RPW;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / S, s = lane - sub * S;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < nwarps;
+       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int row = (int)(w * RPW + sub);
+    const bool ok = row < K.n;
+    double acc = ok ? csr_row_dot<S, double, double, double>(K, x, row, s) : 0.0;
+    if constexpr (S > 1) acc = split_reduce<1, S, double>(acc);
+    if (ok && s == 0) {
+      const double val = MODE == SPMV_RESID ? f[row] - acc : acc;
+      y[row] = val;
+      if (w0) d[0] += val * w0[row];
+      if (self_dot) d[1] += val * val;
+    }
+  }
+  if (reduce) grid_reduce<2>(d, R, slot, op);
+}
+
+// CSR values of K from its block values (after gbs_update_values).
+static __global__ void k_gather_vals(int64_t nnz, const int* __restrict__ map,
+                                     const double* __restrict__ bval, double* __restrict__ cval) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
+       i += (int64_t)gridDim.x * blockDim.x)
+    cval[i] = bval[map[i]];
+}
+
+// flag = 1 if any block value outside the CSR pattern (mask bit set) is nonzero.
+static __global__ void k_check_outside(int64_t nvals, const unsigned* __restrict__ zero_mask,
+                                       const double* __restrict__ bval, int* __restrict__ flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvals;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (((zero_mask[i >> 5] >> (i & 31)) & 1u) && bval[i] != 0.0) *flag = 1;
+}
+
 // p = r + beta (p - omega v), beta = (rho / rho_old) (alpha / omega); p = r on the first step.
 static __global__ void k_bicg_p(int64_t n, const double* __restrict__ r, const double* __restrict__ v,
                          double* __restrict__ p, const double* __restrict__ sc) {

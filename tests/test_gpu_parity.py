@@ -492,3 +492,27 @@ def test_c5_mixed_adjoint_matches_fp64_adjoint(N):
     assert abs(n16 - n64) <= 1e-5 * n64
     assert np.linalg.norm(g16 - g64) <= 1e-4 * n64
     assert abs(grads[gb.GBS_BF16][1] - grads[gb.GBS_FP64][1]) <= 1e-4 * grads[gb.GBS_FP64][1]
+
+
+def test_update_values_outside_csr_pattern_falls_back_to_blocks():
+    """K runs as scalar CSR of its build-time nonzeros; an update that puts
+    a nonzero where a stored block held a zero must still be honoured."""
+    s = si.make_system("c2", N=7)
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, _params(s, relax=gb.GBS_JACOBI))
+    vals = s.data.copy()
+    blk = np.nonzero(s.indices != np.repeat(np.arange(len(s.indptr) - 1), np.diff(s.indptr)))[0][5]
+    assert vals[blk, 0, 1] == 0.0
+    vals[blk, 0, 1] = 0.37 * vals[blk, 0, 0]
+    K2 = bsr.from_arrays(s.indptr, s.indices, vals, 4)
+    x = np.random.default_rng(4).standard_normal(s.n)
+    gb.update_values(H, dev(vals.reshape(-1)))
+    y = host(gb.spmv(H, dev(x)))
+    assert np.all(np.abs(y - K2.scipy() @ x) <= 1e-13 * (abs(K2.scipy()) @ np.abs(x)) + 1e-300)
+    xs, info = gb.solve(H, dev(s.b))
+    assert info.converged
+    assert np.linalg.norm(s.b - K2.scipy() @ host(xs)) / np.linalg.norm(s.b) <= 1e-8
+    # and back: values inside the pattern keep the fast form correct too
+    gb.update_values(H, dev(s.data.reshape(-1)))
+    y = host(gb.spmv(H, dev(x)))
+    K1 = bsr.from_arrays(s.indptr, s.indices, s.data, 4).scipy()
+    assert np.all(np.abs(y - K1 @ x) <= 1e-13 * (abs(K1) @ np.abs(x)) + 1e-300)
