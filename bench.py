@@ -77,11 +77,11 @@ def kernel_source_sha1():
     return h.hexdigest()
 
 
-def profiled_traffic(workload):
-    """DRAM bytes per launch of the outer SpMV from the committed ncu summary
-    profiles/k_outer_n_<workload>.txt, or None when the kernel sources have
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    profiles/<kernel>_<workload>.txt, or None when the kernel sources have
     changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", "k_outer_n_%s.txt" % workload)
+    path = os.path.join(ROOT, "profiles", "%s_%s.txt" % (kernel, workload))
     if not os.path.exists(path):
         return None
     vals = {}
@@ -299,6 +299,12 @@ def main():
     ap.add_argument("--sample-iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--schur-order", type=int, default=0,
+                    help="c3 workloads: 0 full Eq. SchurPC, 1 lower factorisation")
+    ap.add_argument("--schur-p", type=int, default=0,
+                    help="c3 workloads: 0 pressure AMG V-cycle, 1 one SPAI0 application on S_hat")
+    ap.add_argument("--level-format", type=int, default=0,
+                    help="0 scalar CSR for mostly-zero block levels, 1 block form everywhere")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -319,7 +325,10 @@ def main():
     wl = args.workload
     spec = WORKLOADS[wl]
     s = si.make_system(spec["system"])
-    prm = solver_params(gb, wl, use_graph=0 if args.no_graph else 1)
+    extra = {"level_format": args.level_format}
+    if spec["system"] == "c3":
+        extra.update(schur_order=args.schur_order, schur_p=args.schur_p)
+    prm = solver_params(gb, wl, use_graph=0 if args.no_graph else 1, **extra)
     t0 = time.perf_counter()
     H = gb.build_hierarchy(s.indptr, s.indices, s.data, s.bdim, prm)
     torch.cuda.synchronize()
@@ -409,23 +418,26 @@ def main():
     bsr_ms = timed(lambda: gb.spmv_dots_noalloc(rp, ci, va, B, x, y, w=wv))
     spmv_bytes = algorithmic_spmv_bytes(nbr, nnzb, B)
     achieved = spmv_bytes / (bsr_ms * 1e-3) / 1e9
-    traffic = profiled_traffic(wl)
     # FP64 block SpMV does B*B FMAs per stored block; on GB300 the FP64 pipe
-    # (not HBM) is the tighter roofline for this kernel
+    # (not HBM) is the tighter roofline for the block kernel
     flops = 2.0 * nnzb * B * B
     tflops = flops / (bsr_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "k_outer_n (BSR %dx%d FP64 SpMV of K, with two fused dots)" % (B, B),
-                "algorithmic_flops": flops, "ms": bsr_ms,
-                "peak_kind": "nominal FP64 rate (about 2 DFMA/clk/SM x 152 SMs x 2.07 GHz)",
+    bsr_spmv = {"kernel": "k_outer_n (BSR %dx%d FP64 SpMV of K, with two fused dots)" % (B, B),
+                "ms": bsr_ms, "bound": "alu", "achieved_tflops": tflops,
+                "peak_tflops": FP64_PEAK_TFLOPS, "frac": tflops / FP64_PEAK_TFLOPS,
                 "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "algorithmic_bytes": spmv_bytes, "peak_kind": peak_kind}}
-    outer_as_run = {"kernel": "outer SpMV of K as the solve runs it (k_outer_csr on the scalar CSR "
-                              "of K's %d nonzeros when its blocks are at most half nonzero)" % nnz_true,
-                    "ms": spmv_ms,
-                    "algorithmic_bytes": csr_bytes, "achieved_gbs": csr_gbs,
-                    "frac_hbm": csr_gbs / peak}
+                        "algorithmic_bytes": spmv_bytes, "peak_kind": peak_kind},
+                "traffic": profiled_traffic("k_outer_n", wl)}
+    # the dominant kernel of the solve (largest share of the ncu launch list,
+    # profiles/launches_c2_fp64_solve.txt): the outer SpMV as run, timed with
+    # CUDA events on the solve's stream right after the timed region
+    roofline = {"bound": "hbm", "achieved": csr_gbs, "peak": peak, "unit": "GB/s",
+                "frac": csr_gbs / peak, "traffic": profiled_traffic("k_outer_csr", wl),
+                "kernel": "k_outer_csr (FP64 SpMV of K as scalar CSR of its %d nonzeros, "
+                          "two fused dots)" % nnz_true,
+                "algorithmic_bytes": csr_bytes, "ms": spmv_ms, "peak_kind": peak_kind,
+                "fp64": {"achieved_tflops": 2.0 * nnz_true / (spmv_ms * 1e-3) / 1e12,
+                         "peak_tflops": FP64_PEAK_TFLOPS}}
     # the V-cycle as a whole (monolithic AMG only)
     vcycle = None
     if spec["system"] != "c3":
@@ -452,12 +464,12 @@ def main():
         "config": {"workload": spec["desc"], "l2": "inputs larger than L2 (K = %.0f MB)"
                    % (nnzb * (B * B * 8 + 4) / 1e6), "parallelism": "replicas" if world > 1 else "1gpu",
                    "iterations": iters[-1], "rel_res": rel_res, "converged": converged,
-                   "setup_s": setup_s, "graph": not args.no_graph},
+                   "setup_s": setup_s, "graph": not args.no_graph, **extra},
         "e2e": {"value": e2e_ms / world, "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 8),
                 "d2h_bytes_per_step": int(x.numel() * 8)},
         "gpu_launches": int(launches),
         "roofline": roofline,
-        "outer_spmv_as_run": outer_as_run,
+        "bsr_spmv": bsr_spmv,
         "vcycle": vcycle,
         "clocks": clocks,
         "hierarchy_bytes": gb.hierarchy_info(H)["bytes"],

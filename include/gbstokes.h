@@ -102,6 +102,11 @@ typedef struct {
                              half nonzero run as scalar CSR of their nonzeros
                              (same operator, fewer bytes and FMAs); 1: keep
                              every level in block form */
+  int32_t schur_p;        /* Schur pressure solve: 0 one AMG V-cycle on S_hat;
+                             1 one application of the relax_p smoother on S_hat
+                             (Section 4: a single SPAI0 application) */
+  int32_t schur_order;    /* 0 "full" Eq. SchurPC (two velocity solves);
+                             1 "lower" factorisation (one velocity solve) */
 } gbs_params;
 
 typedef struct {

@@ -10,7 +10,13 @@ of the velocity block.  The paper writes B_c and B_c^T for D and G; on
 the finite-difference stand-in D = -G^T.
 
 Read literally, Eq. SchurPC applies the velocity preconditioner twice:
-u* = V_A(r_u), p = V_S(r_p - D u*), u = V_A(r_u - G p).
+u* = V_A(r_u), p = V_S(r_p - D u*), u = V_A(r_u - G p) ("full").
+Variants (the paper's own configurations):
+* pressure solve = one application of the pressure smoother on S_hat
+  (Section 4: one SPAI0 application as the approximation to S^-1, Listing
+  V2's as_preconditioner + preonly) instead of an AMG V-cycle;
+* "lower" ordering (the LOWER factorisation of the PETSc configuration in
+  Section 4): u = V_A(r_u), p = V_S(r_p - D u), one velocity solve.
 """
 from __future__ import annotations
 
@@ -67,12 +73,21 @@ class SchurPrecond:
     split: SchurSplit
     S_hat: Bsr
     HA: amg.Hierarchy
-    HS: amg.Hierarchy
+    HS: amg.Hierarchy | None
+    order: str = "full"            # "full" | "lower"
+    M_S: np.ndarray | None = None  # pressure smoother (used when HS is None)
+
+    def _pressure(self, q, transpose):
+        if self.HS is not None:
+            return amg.vcycle(self.HS, q, 0, transpose)
+        return amg.apply_M(self.M_S, q, transpose)
 
     def apply(self, r: np.ndarray, transpose: bool = False) -> np.ndarray:
-        """Eq. SchurPC with one V-cycle per inner solve.  The transposed
-        application is the same step on K^T = [A^T D^T; G^T C^T] with
-        transposed V-cycles (it equals the exact transpose of ``apply``)."""
+        """Eq. SchurPC with one preconditioner application per inner solve.
+        The transposed application is the exact transpose: for "full" the
+        same steps on K^T = [A^T D^T; G^T C^T] with transposed inner
+        solves; for "lower" the upper-triangular steps p = S'^T r_p,
+        u = A'^T (r_u - D^T p)."""
         nv = self.split.nvel
         rr = r.reshape(-1, nv + 1)
         ru = rr[:, :nv].reshape(-1).copy()
@@ -83,10 +98,17 @@ class SchurPrecond:
         else:
             Dm = self.split.D.scipy()
             Gm = self.split.G.scipy()
-        u1 = amg.vcycle(self.HA, ru, 0, transpose)
-        q = rp - Dm @ u1
-        p = amg.vcycle(self.HS, q, 0, transpose)
-        u = amg.vcycle(self.HA, ru - Gm @ p, 0, transpose)
+        if self.order == "lower" and transpose:
+            p = self._pressure(rp, True)
+            u = amg.vcycle(self.HA, ru - Gm @ p, 0, True)
+        else:
+            u1 = amg.vcycle(self.HA, ru, 0, transpose)
+            q = rp - Dm @ u1
+            p = self._pressure(q, transpose)
+            if self.order == "lower":
+                u = u1
+            else:
+                u = amg.vcycle(self.HA, ru - Gm @ p, 0, transpose)
         z = np.empty_like(rr)
         z[:, :nv] = u.reshape(-1, nv)
         z[:, nv] = p
@@ -94,9 +116,15 @@ class SchurPrecond:
 
 
 def build(K: Bsr, nvel: int = 3, prmA: amg.AmgParams | None = None,
-          prmS: amg.AmgParams | None = None) -> SchurPrecond:
+          prmS: amg.AmgParams | None = None, order: str = "full",
+          pressure: str = "amg") -> SchurPrecond:
+    """pressure: "amg" (V-cycle on S_hat), or "spai0" / "jacobi" (one
+    application of that smoother on S_hat)."""
     S = split(K, nvel)
     Sh = s_hat(S)
     HA = amg.build_hierarchy(S.A, prmA)
-    HS = amg.build_hierarchy(Sh, prmS)
-    return SchurPrecond(S, Sh, HA, HS)
+    if pressure == "amg":
+        return SchurPrecond(S, Sh, HA, amg.build_hierarchy(Sh, prmS), order)
+    prmS = prmS or amg.AmgParams()
+    M = amg.spai0(Sh) if pressure == "spai0" else amg.jacobi(Sh, prmS.jacobi_omega)
+    return SchurPrecond(S, Sh, HA, None, order, M)

@@ -60,6 +60,7 @@ class Params(ctypes.Structure):
         ("smooth_P", ctypes.c_int32), ("power_iters", ctypes.c_int32), ("nvel", ctypes.c_int32),
         ("use_graph", ctypes.c_int32), ("enable_adjoint", ctypes.c_int32),
         ("setup_only", ctypes.c_int32), ("level_format", ctypes.c_int32),
+        ("schur_p", ctypes.c_int32), ("schur_order", ctypes.c_int32),
     ]
 
 

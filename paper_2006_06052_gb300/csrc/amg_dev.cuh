@@ -502,6 +502,21 @@ __global__ void k_schur_u(DevBsr<VT> G, const VT* __restrict__ Gval, bool tr,
     for (int c = 0; c < NV; ++c) fu2[(size_t)i * NV + c] = acc[c];
   }
 }
+// q_i = r_p,i (pressure part of an interleaved vector)
+template <int NV, class ST>
+__global__ void k_gather_p(int nn, const double* __restrict__ r, ST* __restrict__ q) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
+       i += (int64_t)gridDim.x * blockDim.x)
+    q[i] = (ST)r[i * (NV + 1) + NV];
+}
+// p_i = m_i q_i (one application of a scalar pressure smoother)
+template <class VT, class ST>
+__global__ void k_diag_apply(int nn, const VT* __restrict__ m, const ST* __restrict__ q,
+                             ST* __restrict__ p) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = cvt<ST>(m[i]) * q[i];
+}
 template <int NV, class ST>
 __global__ void k_scatter_z(int nn, const ST* __restrict__ u, const ST* __restrict__ p,
                             double* __restrict__ z) {
@@ -521,6 +536,8 @@ struct SchurPrecond final : DevPrecond {
   DevAmg<P> A, S;
   DevBsr<VT> G, D;  // share K's pattern; val = coupling values
   int nv = 3, nn = 0;
+  int order = 0;                 // 0 full, 1 lower
+  const VT* MS = nullptr;        // pressure smoother when the pressure solve is one sweep
   ST *fu = nullptr, *fu2 = nullptr, *u1 = nullptr, *u = nullptr, *q = nullptr, *p = nullptr;
   Arena ar;
   int64_t nnzb = 0;
@@ -530,9 +547,15 @@ struct SchurPrecond final : DevPrecond {
     nv = Hs.nvel;
     nn = Hs.C.nbr;
     nnzb = Hs.C.nnzb();
+    order = o.schur_order;
     A.build(HA, o, s);
-    S.build(HS, o, s);
     std::vector<std::vector<VT>> keep;
+    if (o.schur_p_smoother) {
+      keep.push_back(cast_vec<VT>(Hs.MS));
+      MS = ar.upload(keep.back().data(), keep.back().size(), s);
+    } else {
+      S.build(HS, o, s);
+    }
     G = upload_bsr<VT, AT>(ar, Hs.G, o.tmaps, s, keep);
     D.nbr = Hs.D.nbr;
     D.nbc = Hs.D.nbc;
@@ -550,22 +573,49 @@ struct SchurPrecond final : DevPrecond {
     GBS_CUDA(cudaStreamSynchronize(s));
   }
 
+  void pressure(const ST* qin, ST* pout, bool tr, cudaStream_t s) {
+    if (MS) {
+      k_diag_apply<VT, ST><<<grid_for(nn), 256, 0, s>>>(nn, MS, qin, pout);
+      GBS_LAUNCH_CHECK();
+    } else {
+      S.vcycle(qin, pout, tr, s);
+    }
+  }
+
+  // Forward "full": u1 = V_A(r_u); q = r_p - D u1; p = V_S(q); u = V_A(r_u - G p).
+  // Forward "lower": the same without the second velocity solve (u = u1).
+  // Transposed "full": the same steps with A^T, S^T and G^T, D^T swapped.
+  // Transposed "lower" (upper form on K^T): p = V_S^T(r_p); u = V_A^T(r_u - D^T p).
   template <int NV>
   void run(const double* r, double* z, bool tr, cudaStream_t s) {
     const unsigned g = grid_for((int64_t)nn * NV);
     const unsigned gn = grid_for(nn);
     k_gather_u<NV, ST><<<g, 256, 0, s>>>(nn, r, fu);
     GBS_LAUNCH_CHECK();
-    A.vcycle(fu, u1, tr, s);
-    // forward: q = r_p - D u1; transposed: q = r_p - G^T u1
-    k_schur_q<NV, VT, ST><<<gn, 256, 0, s>>>(D, tr ? G.val : D.val, tr, r, u1, q);
-    GBS_LAUNCH_CHECK();
-    S.vcycle(q, p, tr, s);
-    // forward: fu2 = fu - G p; transposed: fu2 = fu - D^T p
-    k_schur_u<NV, VT, ST><<<gn, 256, 0, s>>>(G, tr ? D.val : G.val, tr, fu, p, fu2);
-    GBS_LAUNCH_CHECK();
-    A.vcycle(fu2, u, tr, s);
-    k_scatter_z<NV, ST><<<grid_for((int64_t)nn * (NV + 1)), 256, 0, s>>>(nn, u, p, z);
+    const ST* uout = u;
+    if (order == 1 && tr) {
+      k_gather_p<NV, ST><<<gn, 256, 0, s>>>(nn, r, q);
+      GBS_LAUNCH_CHECK();
+      pressure(q, p, true, s);
+      k_schur_u<NV, VT, ST><<<gn, 256, 0, s>>>(G, D.val, true, fu, p, fu2);
+      GBS_LAUNCH_CHECK();
+      A.vcycle(fu2, u, true, s);
+    } else {
+      A.vcycle(fu, u1, tr, s);
+      // forward: q = r_p - D u1; transposed: q = r_p - G^T u1
+      k_schur_q<NV, VT, ST><<<gn, 256, 0, s>>>(D, tr ? G.val : D.val, tr, r, u1, q);
+      GBS_LAUNCH_CHECK();
+      pressure(q, p, tr, s);
+      if (order == 1) {
+        uout = u1;
+      } else {
+        // forward: fu2 = fu - G p; transposed: fu2 = fu - D^T p
+        k_schur_u<NV, VT, ST><<<gn, 256, 0, s>>>(G, tr ? D.val : G.val, tr, fu, p, fu2);
+        GBS_LAUNCH_CHECK();
+        A.vcycle(fu2, u, tr, s);
+      }
+    }
+    k_scatter_z<NV, ST><<<grid_for((int64_t)nn * (NV + 1)), 256, 0, s>>>(nn, uout, p, z);
     GBS_LAUNCH_CHECK();
   }
 
@@ -588,7 +638,8 @@ struct SchurPrecond final : DevPrecond {
   }
   double bytes_per_apply() const override {
     const double sv = sizeof(VT), sx = sizeof(ST);
-    double b = 2 * A.bytes_per_cycle() + S.bytes_per_cycle();
+    double b = (order == 1 ? 1 : 2) * A.bytes_per_cycle();
+    b += MS ? nn * (sv + 2 * sx) : S.bytes_per_cycle();
     // gather, two couplings, scatter
     b += nn * nv * (8 + sx);
     b += nnzb * (nv * sv + 4) + nn * nv * sx + nn * (8 + sx);

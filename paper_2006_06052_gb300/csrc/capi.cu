@@ -116,6 +116,8 @@ void check_params(const gbs_params* p) {
   if (p->precond == GBS_PC_SCHUR && (p->nvel < 1 || p->nvel > 3))
     throw SetupError{"nvel must be in 1..3"};
   if (p->level_format < 0 || p->level_format > 1) throw SetupError{"level_format must be 0 or 1"};
+  if (p->schur_p < 0 || p->schur_p > 1) throw SetupError{"schur_p must be 0 or 1"};
+  if (p->schur_order < 0 || p->schur_order > 1) throw SetupError{"schur_order must be 0 or 1"};
 }
 
 AmgSetupParams amg_prm(const gbs_params* p, int relax) {
@@ -137,6 +139,8 @@ PrecondOptions pc_opts(const gbs_params* p) {
   o.npost = p->npost;
   o.tmaps = p->enable_adjoint != 0;
   o.level_format = p->level_format;
+  o.schur_order = p->schur_order;
+  o.schur_p_smoother = p->schur_p == 1;
   return o;
 }
 
@@ -668,6 +672,8 @@ gbs_status gbs_params_default(gbs_params* p) {
   p->enable_adjoint = 1;
   p->setup_only = 0;
   p->level_format = 0;
+  p->schur_p = 0;
+  p->schur_order = 0;
   return GBS_OK;
 }
 
@@ -690,7 +696,10 @@ gbs_status gbs_build_hierarchy(const gbs_bsr* A, const gbs_params* params, void*
       if (K.br != params->nvel + 1) throw SetupError{"Schur needs bdim = nvel + 1"};
       h.Sh = schur_split(K, params->nvel);
       h.HA = build_amg(h.Sh.A, amg_prm(params, params->relax));
-      h.HS = build_amg(h.Sh.S, amg_prm(params, params->relax_p));
+      if (params->schur_p == 1)
+        h.Sh.MS = params->relax_p == GBS_SPAI0 ? spai0(h.Sh.S) : jacobi(h.Sh.S, params->jacobi_omega);
+      else
+        h.HS = build_amg(h.Sh.S, amg_prm(params, params->relax_p));
     } else {
       h.H = build_amg(K, amg_prm(params, params->relax));
     }
@@ -849,6 +858,8 @@ gbs_status gbs_hierarchy_info(const gbs_hierarchy* hh, int32_t which, int32_t* n
     if (!hh || !nlevels) throw SetupError{"null argument"};
     const Handle& h = hh->h;
     if (which < 0 || which > 1 || (which == 1 && !h.schur)) throw SetupError{"bad hierarchy id"};
+    if (which == 1 && h.prm.schur_p == 1)
+      throw SetupError{"the pressure solve is one smoother application (no pressure AMG)"};
     const HAmg& H = h.schur ? (which == 0 ? h.HA : h.HS) : h.H;
     const int nl = (int)H.levels.size() + 1;
     *nlevels = nl;
@@ -878,6 +889,8 @@ gbs_status gbs_export_level(const gbs_hierarchy* hh, int32_t which, int32_t leve
     if (!hh || !n_brows || !n_bcols || !nnzb) throw SetupError{"null argument"};
     const Handle& h = hh->h;
     if (which < 0 || which > 1 || (which == 1 && !h.schur)) throw SetupError{"bad hierarchy id"};
+    if (which == 1 && h.prm.schur_p == 1)
+      throw SetupError{"the pressure solve is one smoother application (no pressure AMG)"};
     const HAmg& H = h.schur ? (which == 0 ? h.HA : h.HS) : h.H;
     const int nl = (int)H.levels.size() + 1;
     if (level < 0 || level >= nl) throw SetupError{"bad level"};

@@ -82,6 +82,8 @@ struct PrecondOptions {
   int npre = 1, npost = 1;
   bool tmaps = true;
   int level_format = 0;  // 0: scalar CSR for levels whose blocks are mostly zeros; 1: always blocks
+  int schur_order = 0;   // 0 full (two velocity solves), 1 lower (one)
+  bool schur_p_smoother = false;  // pressure solve = one smoother application (HSchur::MS)
 };
 
 std::unique_ptr<DevPrecond> make_amg_precond(const HAmg& H, const PrecondOptions& o,

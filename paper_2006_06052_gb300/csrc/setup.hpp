@@ -76,6 +76,7 @@ double block_fill(const HBsr& A);
 struct HSchur {
   HBsr A, G, D, C, S;
   int nvel = 3;
+  std::vector<double> MS;   // pressure smoother on S (when the pressure solve is one sweep)
 };
 HSchur schur_split(const HBsr& K, int nvel);
 
