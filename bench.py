@@ -58,8 +58,8 @@ def solver_params(gb, wl, **kw):
     name = WORKLOADS[wl]["system"]
     prec = WORKLOADS[wl]["precision"]
     if name == "c3":
-        return gb.params_default(precond=gb.GBS_PC_SCHUR, krylov=gb.GBS_GMRES, precision=prec,
-                                 enable_adjoint=0, **kw)
+        kw.setdefault("krylov", gb.GBS_GMRES)
+        return gb.params_default(precond=gb.GBS_PC_SCHUR, precision=prec, enable_adjoint=0, **kw)
     relax = gb.GBS_SPAI0 if name == "c1" else gb.GBS_JACOBI
     return gb.params_default(relax=relax, precision=prec, enable_adjoint=0, **kw)
 
@@ -303,6 +303,8 @@ def main():
                     help="c3 workloads: 0 full Eq. SchurPC, 1 lower factorisation")
     ap.add_argument("--schur-p", type=int, default=0,
                     help="c3 workloads: 0 pressure AMG V-cycle, 1 one SPAI0 application on S_hat")
+    ap.add_argument("--krylov", default=None, choices=["bicgstab", "gmres", "idrs"],
+                    help="outer solver (default: the workload's: BiCGStab for c1/c2, GMRES(30) for c3)")
     ap.add_argument("--level-format", type=int, default=0,
                     help="0 scalar CSR for mostly-zero block levels, 1 block form everywhere")
     args = ap.parse_args()
@@ -326,6 +328,9 @@ def main():
     spec = WORKLOADS[wl]
     s = si.make_system(spec["system"])
     extra = {"level_format": args.level_format}
+    if args.krylov:
+        extra["krylov"] = {"bicgstab": gb.GBS_BICGSTAB, "gmres": gb.GBS_GMRES,
+                           "idrs": gb.GBS_IDRS}[args.krylov]
     if spec["system"] == "c3":
         extra.update(schur_order=args.schur_order, schur_p=args.schur_p)
     prm = solver_params(gb, wl, use_graph=0 if args.no_graph else 1, **extra)

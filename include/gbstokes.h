@@ -5,7 +5,8 @@
  *
  * The library solves K x = b, K a square matrix stored as CSR or block
  * CSR (BSR) with bdim x bdim blocks, with a right-preconditioned Krylov
- * method (BiCGStab or restarted GMRES) and one of two preconditioners:
+ * method (BiCGStab, restarted GMRES, or IDR(s) -- the paper's outer
+ * solver, Section 4 Listings V1/V2) and one of two preconditioners:
  *   - a monolithic smoothed-aggregation AMG V-cycle with SPAI0 or damped
  *     Jacobi relaxation (Section 2.1, Listing "composition");
  *   - the Schur pressure-correction preconditioner of Section 4,
@@ -53,7 +54,7 @@ typedef enum {
 } gbs_status;
 
 enum { GBS_PC_AMG = 0, GBS_PC_SCHUR = 1 };
-enum { GBS_BICGSTAB = 0, GBS_GMRES = 1 };
+enum { GBS_BICGSTAB = 0, GBS_GMRES = 1, GBS_IDRS = 2 };
 enum { GBS_FP64 = 0, GBS_FP32 = 1, GBS_BF16 = 2 };
 enum { GBS_SPAI0 = 0, GBS_JACOBI = 1 };
 
@@ -78,7 +79,7 @@ typedef struct {
  * fields.  Obtain defaults with gbs_params_default(). */
 typedef struct {
   int32_t precond;        /* GBS_PC_AMG | GBS_PC_SCHUR */
-  int32_t krylov;         /* GBS_BICGSTAB | GBS_GMRES */
+  int32_t krylov;         /* GBS_BICGSTAB | GBS_GMRES | GBS_IDRS */
   int32_t restart;        /* GMRES restart length m (default 30, max 64) */
   double tol;             /* relative true residual ||b-Kx||/||b|| (1e-8) */
   int32_t maxiter;        /* default 1000 */
@@ -107,6 +108,10 @@ typedef struct {
                              (Section 4: a single SPAI0 application) */
   int32_t schur_order;    /* 0 "full" Eq. SchurPC (two velocity solves);
                              1 "lower" factorisation (one velocity solve) */
+  int32_t idr_s;          /* IDR(s) shadow-space dimension (5, as the paper's
+                             solvers; 1..8).  The shadow space is SplitMix64
+                             (seed idr_seed) orthonormalised by MGS */
+  int32_t idr_seed;
 } gbs_params;
 
 typedef struct {

@@ -21,13 +21,13 @@ __all__ = [
     "GbsError", "Params", "Info", "Hierarchy", "params_default", "build_hierarchy",
     "import_hierarchy", "solve", "solve_adjoint", "sampled_outer", "update_values", "spmv",
     "apply_precond", "hierarchy_info", "export_level", "export_level_sizes", "spmv_dots_noalloc", "precond_bytes", "load_library", "build", "kernel_launches",
-    "GBS_PC_AMG", "GBS_PC_SCHUR", "GBS_BICGSTAB", "GBS_GMRES", "GBS_FP64", "GBS_FP32",
+    "GBS_PC_AMG", "GBS_PC_SCHUR", "GBS_BICGSTAB", "GBS_GMRES", "GBS_IDRS", "GBS_FP64", "GBS_FP32",
     "GBS_BF16", "GBS_SPAI0", "GBS_JACOBI", "EXPORTED",
 ]
 
 GBS_OK, GBS_NOT_CONVERGED = 0, 1
 GBS_PC_AMG, GBS_PC_SCHUR = 0, 1
-GBS_BICGSTAB, GBS_GMRES = 0, 1
+GBS_BICGSTAB, GBS_GMRES, GBS_IDRS = 0, 1, 2
 GBS_FP64, GBS_FP32, GBS_BF16 = 0, 1, 2
 GBS_SPAI0, GBS_JACOBI = 0, 1
 
@@ -61,6 +61,7 @@ class Params(ctypes.Structure):
         ("use_graph", ctypes.c_int32), ("enable_adjoint", ctypes.c_int32),
         ("setup_only", ctypes.c_int32), ("level_format", ctypes.c_int32),
         ("schur_p", ctypes.c_int32), ("schur_order", ctypes.c_int32),
+        ("idr_s", ctypes.c_int32), ("idr_seed", ctypes.c_int32),
     ]
 
 

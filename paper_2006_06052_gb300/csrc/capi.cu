@@ -54,6 +54,7 @@ struct Handle {
   // work vectors
   double *r, *rhat, *p, *ph, *v, *s, *sh, *t, *xi, *bi;
   double *V = nullptr, *hcol, *hcol2, *ydev, *z, *u;
+  double *Pidr = nullptr, *Gidr = nullptr, *Uidr = nullptr;  // IDR(s): s x n each
   int m = 30;
   double* sc;
   double* sc_host = nullptr;     // pinned
@@ -77,6 +78,8 @@ struct Handle {
 namespace {
 
 cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+std::vector<double> idr_shadow_space(int64_t n, int s, uint64_t seed);
 
 unsigned vgrid(int64_t n) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
@@ -103,7 +106,9 @@ HBsr from_c(const gbs_bsr* A) {
 void check_params(const gbs_params* p) {
   if (!p) throw SetupError{"null params"};
   if (p->precond != GBS_PC_AMG && p->precond != GBS_PC_SCHUR) throw SetupError{"bad precond"};
-  if (p->krylov != GBS_BICGSTAB && p->krylov != GBS_GMRES) throw SetupError{"bad krylov"};
+  if (p->krylov != GBS_BICGSTAB && p->krylov != GBS_GMRES && p->krylov != GBS_IDRS)
+    throw SetupError{"bad krylov"};
+  if (p->krylov == GBS_IDRS && (p->idr_s < 1 || p->idr_s > 8)) throw SetupError{"idr_s must be in 1..8"};
   if (p->restart < 1 || p->restart > 64) throw SetupError{"restart must be in 1..64"};
   if (!(p->tol > 0.0)) throw SetupError{"tol must be > 0"};
   if (p->maxiter < 1) throw SetupError{"maxiter must be >= 1"};
@@ -205,6 +210,13 @@ void alloc_work(Handle& h, cudaStream_t s) {
     h.V = a.alloc<double>((size_t)(h.m + 1) * n);
     h.z = a.alloc<double>(n);
     h.u = a.alloc<double>(n);
+  }
+  if (h.prm.krylov == GBS_IDRS) {
+    const int sdim = h.prm.idr_s;
+    std::vector<double> P = idr_shadow_space(n, sdim, (uint64_t)(uint32_t)h.prm.idr_seed);
+    h.Pidr = a.upload(P.data(), P.size(), s);
+    h.Gidr = a.alloc<double>((size_t)sdim * n);
+    h.Uidr = a.alloc<double>((size_t)sdim * n);
   }
   h.hcol = a.alloc<double>(MAX_DOTS);
   h.hcol2 = a.alloc<double>(MAX_DOTS);
@@ -439,6 +451,36 @@ gbs_status solve_bicgstab(Handle& h, const double* b, double* x, bool tr, cudaSt
   return st;
 }
 
+// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator.
+inline uint64_t splitmix64(uint64_t counter, uint64_t seed) {
+  uint64_t z = seed + (counter + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// s orthonormal shadow vectors (rows): entry (j, i) = u - 1/2, u the top
+// 53 bits of splitmix64(j*n + i) over 2^53, then modified Gram-Schmidt.
+std::vector<double> idr_shadow_space(int64_t n, int s, uint64_t seed) {
+  std::vector<double> P((size_t)s * n);
+  for (int64_t c = 0; c < (int64_t)s * n; ++c)
+    P[c] = (double)(splitmix64((uint64_t)c, seed) >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  for (int j = 0; j < s; ++j) {
+    double* pj = &P[(size_t)j * n];
+    for (int i = 0; i < j; ++i) {
+      const double* pi = &P[(size_t)i * n];
+      double d = 0.0;
+      for (int64_t e = 0; e < n; ++e) d += pi[e] * pj[e];
+      for (int64_t e = 0; e < n; ++e) pj[e] -= d * pi[e];
+    }
+    double nrm = 0.0;
+    for (int64_t e = 0; e < n; ++e) nrm += pj[e] * pj[e];
+    nrm = std::sqrt(nrm);
+    for (int64_t e = 0; e < n; ++e) pj[e] /= nrm;
+  }
+  return P;
+}
+
 void givens(double a, double b, double& c, double& sn) {
   if (b == 0.0) {
     c = 1.0;
@@ -566,6 +608,162 @@ void settle_k_format(Handle& h, cudaStream_t s) {
   if (flag) h.k_csr = false;
 }
 
+// Right-preconditioned IDR(s), bi-orthogonal variant (van Gijzen & Sonneveld
+// 2011): s inner steps keep the residual orthogonal to the shadow space P,
+// then a minimal-residual dimension-reduction step ("maintaining
+// convergence" omega, kappa = 0.7).  The small s x s systems live on the
+// host; every vector operation is a device kernel.  Iterations count
+// applications of K.
+gbs_status solve_idrs(Handle& h, const double* b, double* x, bool tr, cudaStream_t s,
+                      gbs_info* info) {
+  const int64_t n = h.n;
+  const int sd = h.prm.idr_s;
+  const unsigned g = vgrid(n);
+  std::vector<double> hist;
+  GBS_CUDA(cudaEventRecord(h.ev0, s));
+  GBS_CUDA(cudaMemcpyAsync(h.bi, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  GBS_CUDA(cudaMemcpyAsync(h.xi, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
+  GBS_LAUNCH_CHECK();
+  outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, 1, 4, FIN_RR, true, s);
+  read_scalars(h, s);
+  const double bb = h.sc_host[S_BB];
+  if (!std::isfinite(bb)) {
+    g_err = "NaN or Inf in b";
+    return GBS_ERR_NAN;
+  }
+  if (bb == 0.0) {
+    GBS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    return finish(h, info, 0, 0, 0.0, true, hist, s);
+  }
+  const double nb = std::sqrt(bb);
+  double rel = std::sqrt(h.sc_host[S_RR]) / nb;
+  int it = 0, repl = 0;
+  bool conv = rel <= h.prm.tol, breakdown = false;
+  GBS_CUDA(cudaMemsetAsync(h.Gidr, 0, sizeof(double) * n * sd, s));
+  GBS_CUDA(cudaMemsetAsync(h.Uidr, 0, sizeof(double) * n * sd, s));
+  std::vector<double> Mm((size_t)sd * sd, 0.0), f(sd), c(sd), d(sd), al(sd);
+  for (int i = 0; i < sd; ++i) Mm[(size_t)i * sd + i] = 1.0;
+  double om = 1.0;
+  double cur = rel;  // relative norm of the current residual r
+  auto MM = [&](int i, int j) -> double& { return Mm[(size_t)i * sd + j]; };
+  auto rownorm = [&]() {
+    read_scalars(h, s);
+    return std::sqrt(h.sc_host[S_RR]) / nb;
+  };
+  // confirm a recurrence claim with the true residual (which replaces r)
+  auto confirm = [&](double res) {
+    hist.push_back(res);
+    cur = res;
+    if (!(res <= h.prm.tol)) return false;
+    outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, 1, 4, FIN_RR, true, s);
+    ++repl;
+    rel = rownorm();
+    cur = rel;
+    return rel <= h.prm.tol;
+  };
+  auto multidot_P = [&](const double* w, std::vector<double>& out) {
+    k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.Pidr, sd, w, h.hcol, h.red, 5, nullptr);
+    GBS_LAUNCH_CHECK();
+    GBS_CUDA(cudaMemcpyAsync(h.h_host, h.hcol, sizeof(double) * sd, cudaMemcpyDeviceToHost, s));
+    GBS_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < sd; ++i) out[i] = h.h_host[i];
+  };
+  while (!conv && it < h.prm.maxiter && !breakdown) {
+    multidot_P(h.r, f);
+    for (int k = 0; k < sd && !conv && it < h.prm.maxiter; ++k) {
+      for (int i = 0; i < sd - k; ++i) {  // lower-triangular Mm[k:, k:] c = f[k:]
+        double acc = f[k + i];
+        for (int j = 0; j < i; ++j) acc -= MM(k + i, k + j) * c[j];
+        c[i] = acc / MM(k + i, k + i);
+      }
+      Coefs cn{}, cp{};
+      for (int i = 0; i < sd - k; ++i) {
+        cn.c[i] = -c[i];
+        cp.c[i] = c[i];
+      }
+      double* Gk = h.Gidr + (size_t)k * n;
+      double* Uk = h.Uidr + (size_t)k * n;
+      k_idr_comb<<<g, 256, 0, s>>>(n, h.v, 1.0, h.r, Gk, sd - k, cn);   // v = r - G[k:] c
+      GBS_LAUNCH_CHECK();
+      h.pc->apply(h.v, h.ph, tr, s);                                   // v = M^-1 v
+      k_idr_comb<<<g, 256, 0, s>>>(n, Uk, om, h.ph, Uk, sd - k, cp);    // U_k = U[k:] c + om v
+      GBS_LAUNCH_CHECK();
+      outer(h, tr, SPMV_SET, Uk, nullptr, Gk, nullptr, 0, 0, FIN_STORE, false, s);  // G_k = K U_k
+      ++it;
+      multidot_P(Gk, d);
+      for (int i = 0; i < k; ++i) {  // bi-orthogonalise G_k against P[:k]
+        double acc = d[i];
+        for (int j = 0; j < i; ++j) acc -= MM(i, j) * al[j];
+        al[i] = acc / MM(i, i);
+      }
+      if (k > 0) {
+        Coefs ca{};
+        for (int i = 0; i < k; ++i) ca.c[i] = -al[i];
+        k_idr_comb<<<g, 256, 0, s>>>(n, Gk, 1.0, Gk, h.Gidr, k, ca);
+        GBS_LAUNCH_CHECK();
+        k_idr_comb<<<g, 256, 0, s>>>(n, Uk, 1.0, Uk, h.Uidr, k, ca);
+        GBS_LAUNCH_CHECK();
+      }
+      for (int i = k; i < sd; ++i) {
+        double acc = d[i];
+        for (int j = 0; j < k; ++j) acc -= MM(i, j) * al[j];
+        MM(i, k) = acc;
+      }
+      if (MM(k, k) == 0.0) {
+        breakdown = true;
+        break;
+      }
+      const double beta = f[k] / MM(k, k);
+      k_idr_update<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.r, h.xi, Gk, Uk, beta, h.red, 4);
+      GBS_LAUNCH_CHECK();
+      const double res = rownorm();
+      if (!std::isfinite(res)) {
+        rel = res;
+        breakdown = true;
+        break;
+      }
+      if (confirm(res)) {
+        conv = true;
+        break;
+      }
+      for (int i = k + 1; i < sd; ++i) f[i] -= beta * MM(i, k);
+    }
+    if (conv || breakdown || it >= h.prm.maxiter) break;
+    h.pc->apply(h.r, h.ph, tr, s);                                     // v = M^-1 r
+    outer(h, tr, SPMV_SET, h.ph, nullptr, h.t, h.r, 1, 1, FIN_STORE, true, s);  // t = K v, t.r, t.t
+    ++it;
+    read_scalars(h, s);
+    const double ts = h.sc_host[S_D0], tt = h.sc_host[S_D1];
+    om = tt > 0.0 ? ts / tt : 0.0;
+    // ||r|| of the current residual for the kappa rule
+    const double rn = cur * nb;
+    const double rho = (tt > 0.0 && rn > 0.0) ? std::fabs(ts) / (std::sqrt(tt) * rn) : 0.0;
+    if (rho > 0.0 && rho < 0.7) om = om * 0.7 / rho;
+    if (om == 0.0 || !std::isfinite(om)) {
+      breakdown = true;
+      break;
+    }
+    k_idr_update<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.r, h.xi, h.t, h.ph, om, h.red, 4);
+    GBS_LAUNCH_CHECK();
+    const double res = rownorm();
+    if (confirm(res)) conv = true;
+    else rel = cur;
+  }
+  if (!conv) {
+    outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, 1, 4, FIN_RR, true, s);
+    rel = rownorm();
+    conv = rel <= h.prm.tol;
+  }
+  GBS_CUDA(cudaMemcpyAsync(x, h.xi, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  gbs_status st = finish(h, info, it, repl, rel, conv, hist, s);
+  if (breakdown && !conv && st == GBS_NOT_CONVERGED) {
+    g_err = "IDR(s) breakdown";
+    return GBS_ERR_BREAKDOWN;
+  }
+  return st;
+}
+
 gbs_status solve(Handle& h, const double* b, double* x, bool tr, cudaStream_t s, gbs_info* info) {
   need_device(h);
   settle_k_format(h, s);
@@ -574,6 +772,7 @@ gbs_status solve(Handle& h, const double* b, double* x, bool tr, cudaStream_t s,
   need_aligned(x, "x");
   if (tr && !h.prm.enable_adjoint) throw SetupError{"hierarchy was built without enable_adjoint"};
   if (h.prm.krylov == GBS_GMRES) return solve_gmres(h, b, x, tr, s, info);
+  if (h.prm.krylov == GBS_IDRS) return solve_idrs(h, b, x, tr, s, info);
   return solve_bicgstab(h, b, x, tr, s, info);
 }
 
@@ -674,6 +873,8 @@ gbs_status gbs_params_default(gbs_params* p) {
   p->level_format = 0;
   p->schur_p = 0;
   p->schur_order = 0;
+  p->idr_s = 5;
+  p->idr_seed = 0;
   return GBS_OK;
 }
 

@@ -302,6 +302,41 @@ static __global__ void k_set_restart(double* sc) {
   sc[S_FIRST] = 1.0;
 }
 
+// ------------------------------------------------------------------ IDR(s)
+struct Coefs {
+  double c[8];
+};
+
+// out = alpha * a + sum_{i<m} c_i V_i  (V_i = V + i*n).  out may alias a
+// or V_0: every element reads its inputs before writing.
+static __global__ void k_idr_comb(int64_t n, double* out, double alpha, const double* a,
+                                  const double* V, int m, Coefs c) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = a ? alpha * a[e] : 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (i < m) acc += c.c[i] * V[(size_t)i * n + e];
+    out[e] = acc;
+  }
+}
+
+// r -= beta g; x += beta u; sc[S_RR] = r . r
+static __global__ void __launch_bounds__(RED_THREADS, 4)
+    k_idr_update(int64_t n, double* __restrict__ r, double* __restrict__ x,
+                 const double* __restrict__ g, const double* __restrict__ u, double beta, Red R,
+                 int slot) {
+  double d[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = r[i] - beta * g[i];
+    r[i] = ri;
+    x[i] += beta * u[i];
+    d[1] += ri * ri;
+  }
+  grid_reduce<2>(d, R, slot, FIN_RR);
+}
+
 // ------------------------------------------------------------------ GMRES
 // h[i] = V_i . w for i < J (chunks of 8 vectors), and sc[S_WW0] = w . w.
 // gate: if non-null and *gate == 0 the kernel does nothing.

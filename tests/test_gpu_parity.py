@@ -542,3 +542,33 @@ def test_schur_variants_apply_and_solve(order, schur_p):
     x, info = gb.solve(H, dev(s.b))
     assert info.converged and _true_rel(s, host(x)) <= 1e-8
     assert abs(info.iters - io.iters) <= max(1, math.ceil(0.1 * io.iters)), (info.iters, io.iters)
+
+
+@pytest.mark.parametrize("case", ["c2_amg", "c3_schur"])
+def test_idrs_solve_matches_oracle(case):
+    """IDR(5), the paper's outer solver: converges to the 1e-8 true residual
+    within +-10% of the oracle's matvec count, forward and adjoint."""
+    if case == "c2_amg":
+        s = si.make_system("c2", N=13)
+        K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+        Ho = amg.build_hierarchy(K, amg.AmgParams(relax="jacobi"))
+        Mo, MoT = (lambda v: amg.vcycle(Ho, v)), (lambda v: amg.vcycle(Ho, v, 0, True))
+        p = gb.params_default(krylov=gb.GBS_IDRS, relax=gb.GBS_JACOBI)
+    else:
+        s = si.make_system("c3", N=12)
+        K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+        pc = schur.build(K, 3)
+        Mo, MoT = pc.apply, (lambda v: pc.apply(v, transpose=True))
+        p = gb.params_default(krylov=gb.GBS_IDRS, precond=gb.GBS_PC_SCHUR)
+    Ks = K.scipy()
+    xo, io = krylov.idrs(lambda v: Ks @ v, Mo, s.b, s=5, tol=1e-8)
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, p)
+    x, info = gb.solve(H, dev(s.b))
+    assert info.converged and _true_rel(s, host(x)) <= 1e-8
+    assert abs(info.iters - io.iters) <= max(2, math.ceil(0.1 * io.iters)), (info.iters, io.iters)
+    g = np.random.default_rng(2).standard_normal(s.n)
+    lo, ilo = krylov.idrs(lambda v: Ks.T @ v, MoT, g, s=5, tol=1e-8)
+    lam, il = gb.solve_adjoint(H, dev(g))
+    assert il.converged
+    assert np.linalg.norm(g - Ks.T @ host(lam)) / np.linalg.norm(g) <= 1e-8
+    assert abs(il.iters - ilo.iters) <= max(2, math.ceil(0.1 * ilo.iters)), (il.iters, ilo.iters)
