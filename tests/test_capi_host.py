@@ -154,3 +154,18 @@ def test_setup_only_handle_refuses_device_calls():
     H = _host(s)
     info = gb.hierarchy_info(H)
     assert info["bytes"] == 0 and info["nlevels"] >= 1
+
+
+def test_host_setup_plain_aggregation_matches_oracle():
+    """smooth_P = 0: plain (unsmoothed) aggregation, P = P_tent (the
+    paper's velocity AMG in its V2-V4 solvers)."""
+    s = si.make_system("c3", N=7)
+    K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    po = amg.AmgParams(coarse_enough=40, smooth_P=False)
+    pc = schur.build(K, 3, po, po)
+    Hc = _host(s, precond=gb.GBS_PC_SCHUR, krylov=gb.GBS_GMRES, coarse_enough=40, smooth_P=0)
+    _cmp_hierarchy(Hc, 0, pc.HA, 3)
+    _cmp_hierarchy(Hc, 1, pc.HS, 1)
+    ptr, col, val, nbc = gb.export_level(Hc, 0, 0, 1)
+    assert np.all(np.diff(ptr) == 1)                       # one block per row
+    np.testing.assert_array_equal(val, np.broadcast_to(np.eye(3), val.shape))

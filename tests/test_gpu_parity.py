@@ -572,3 +572,21 @@ def test_idrs_solve_matches_oracle(case):
     assert il.converged
     assert np.linalg.norm(g - Ks.T @ host(lam)) / np.linalg.norm(g) <= 1e-8
     assert abs(il.iters - ilo.iters) <= max(2, math.ceil(0.1 * ilo.iters)), (il.iters, ilo.iters)
+
+
+def test_plain_aggregation_solves():
+    """smooth_P = 0 (plain aggregation) for the Schur velocity/pressure AMG:
+    V-cycle parity on the oracle's hierarchy and a converged solve."""
+    s = si.make_system("c3", N=12)
+    K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    po = amg.AmgParams(smooth_P=False, coarse_enough=60)
+    pc = schur.build(K, 3, po, po)
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
+                           _params(s, smooth_P=0, coarse_enough=60))
+    r = np.random.default_rng(31).standard_normal(K.shape[0])
+    assert rel_inf(host(gb.apply_precond(H, dev(r))), pc.apply(r)) <= 1e-10
+    Ks = K.scipy()
+    xo, io = krylov.gmres(lambda v: Ks @ v, pc.apply, s.b, m=30, tol=1e-8)
+    x, info = gb.solve(H, dev(s.b))
+    assert info.converged and _true_rel(s, host(x)) <= 1e-8
+    assert abs(info.iters - io.iters) <= max(1, math.ceil(0.1 * io.iters))

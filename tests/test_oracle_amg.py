@@ -235,3 +235,11 @@ def test_two_grid_contracts_on_poisson():
     V = amg.vcycle_dense(H)
     E = np.eye(63) - V @ A.dense()
     assert np.abs(np.linalg.eigvals(E)).max() < 0.9
+
+
+def test_plain_aggregation_prolongator_is_tentative():
+    A = stokes_bsr(4)
+    H = amg.build_hierarchy(A, amg.AmgParams(coarse_enough=30, smooth_P=False, relax="jacobi"))
+    for lev in H.levels:
+        Pt = amg.tentative_P(lev.agg, lev.P.n_bcols, 4)
+        np.testing.assert_array_equal(lev.P.dense(), Pt.dense())
