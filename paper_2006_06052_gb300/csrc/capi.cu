@@ -605,7 +605,15 @@ void settle_k_format(Handle& h, cudaStream_t s) {
   GBS_CUDA(cudaMemcpyAsync(&flag, h.kflag, sizeof(int), cudaMemcpyDeviceToHost, s));
   GBS_CUDA(cudaStreamSynchronize(s));
   h.k_check_pending = false;
-  if (flag) h.k_csr = false;
+  if (flag) {
+    h.k_csr = false;
+    // captured iterations launch the CSR kernel: capture again
+    for (int i = 0; i < 2; ++i)
+      if (h.gexec[i]) {
+        cudaGraphExecDestroy(h.gexec[i]);
+        h.gexec[i] = nullptr;
+      }
+  }
 }
 
 // Right-preconditioned IDR(s), bi-orthogonal variant (van Gijzen & Sonneveld
