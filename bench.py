@@ -41,6 +41,12 @@ WORKLOADS = {
     "c2": dict(system="c2", precision=0, desc=(
         "3D FD Stokes N=64 (1,048,576 unknowns), lognormal mu sigma=0.5, 4x4 BSR FP64, "
         "monolithic block SA-AMG (damped Jacobi 1+1) + BiCGStab, tol 1e-8")),
+    "c2-fp32": dict(system="c2", precision=1, desc=(
+        "same as c2 with an FP32 hierarchy (FP64 outer BiCGStab, dots and residual "
+        "replacement)")),
+    "c2-bf16": dict(system="c2", precision=2, desc=(
+        "same as c2 with a BF16 hierarchy (FP32 accumulation; FP64 outer BiCGStab, dots and "
+        "residual replacement)")),
     "c1": dict(system="c1", precision=0, desc=(
         "3D FD Stokes N=16 (16,384 unknowns), mu=1, scalar CSR FP64, SA-AMG (SPAI0 1+1) + "
         "BiCGStab, tol 1e-8")),
@@ -432,14 +438,17 @@ def main():
                 "peak_tflops": FP64_PEAK_TFLOPS, "frac": tflops / FP64_PEAK_TFLOPS,
                 "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "algorithmic_bytes": spmv_bytes, "peak_kind": peak_kind},
-                "traffic": profiled_traffic("k_outer_n", wl)}
+                "traffic": profiled_traffic("k_outer_n", spec["system"])}
     # the dominant kernel of the solve (largest share of the ncu launch list,
     # profiles/launches_c2_fp64_solve.txt): the outer SpMV as run, timed with
     # CUDA events on the solve's stream right after the timed region
+    kform, kstored = gb.outer_format(H)
+    kname = {"block": "k_outer_n", "csr": "k_outer_csr"}[kform]
+    kdesc = {"block": "as %dx%d blocks" % (B, B),
+             "csr": "as scalar CSR of its %d nonzeros" % nnz_true}[kform]
     roofline = {"bound": "hbm", "achieved": csr_gbs, "peak": peak, "unit": "GB/s",
-                "frac": csr_gbs / peak, "traffic": profiled_traffic("k_outer_csr", wl),
-                "kernel": "k_outer_csr (FP64 SpMV of K as scalar CSR of its %d nonzeros, "
-                          "two fused dots)" % nnz_true,
+                "frac": csr_gbs / peak, "traffic": profiled_traffic(kname, spec["system"]),
+                "kernel": "%s (FP64 SpMV of K %s)" % (kname, kdesc),
                 "algorithmic_bytes": csr_bytes, "ms": spmv_ms, "peak_kind": peak_kind,
                 "fp64": {"achieved_tflops": 2.0 * nnz_true / (spmv_ms * 1e-3) / 1e12,
                          "peak_tflops": FP64_PEAK_TFLOPS}}

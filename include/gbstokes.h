@@ -99,10 +99,14 @@ typedef struct {
   int32_t enable_adjoint; /* 1: build transpose maps for solve_adjoint */
   int32_t setup_only;     /* 1: build the host hierarchy only (no device work,
                              no GPU needed); export/info work, solves do not */
-  int32_t level_format;   /* 0: hierarchy levels whose stored blocks are at most
-                             half nonzero run as scalar CSR of their nonzeros
-                             (same operator, fewer bytes and FMAs); 1: keep
-                             every level in block form */
+  int32_t level_format;   /* 0: hierarchy levels (and K) whose stored blocks are
+                             at most half nonzero run as scalar CSR of their
+                             nonzeros (same operator, fewer bytes and FMAs);
+                             hierarchy levels among them in 32-node component
+                             slices where that pads at most 10%; 1: keep every
+                             level in block form; 2: plain scalar CSR wherever
+                             blocks are not 1x1; 3: as 2, hierarchy levels in
+                             slices */
   int32_t schur_p;        /* Schur pressure solve: 0 one AMG V-cycle on S_hat;
                              1 one application of the relax_p smoother on S_hat
                              (Section 4: a single SPAI0 application) */
@@ -198,6 +202,14 @@ gbs_status gbs_hierarchy_info(const gbs_hierarchy* h, int32_t which, int32_t* nl
  * indices and vectors of every kernel it launches, from the formats the
  * hierarchy is stored in).  Used for bandwidth reporting. */
 gbs_status gbs_precond_bytes(const gbs_hierarchy* h, double* bytes_per_apply);
+
+/* Layout the FP64 outer SpMV of K runs in now (no counterpart in the
+ * paper; the library's per-operator format choice): *format = 0 block
+ * CSR, 1 scalar CSR of K's build-time nonzeros.  *stored: value entries
+ * the kernel streams (stored block values or nonzeros).  Host only;
+ * reflects a pending fall-back to blocks only after the next solve or
+ * spmv. */
+gbs_status gbs_outer_format(const gbs_hierarchy* h, int32_t* format, int64_t* stored);
 
 /* Copy level l (0 = finest) of AMG `which` to host arrays.  part: 0 = A,
  * 1 = P, 2 = R, 3 = smoother blocks M (row_ptr/col_idx untouched),

@@ -40,6 +40,7 @@ EXPORTED = [
     "gbs_sampled_outer", "gbs_update_values", "gbs_spmv", "gbs_apply_precond",
     "gbs_hierarchy_info", "gbs_export_level", "gbs_import_hierarchy", "gbs_destroy",
     "gbs_last_error", "gbs_kernel_launches", "gbs_spmv_dots_noalloc", "gbs_precond_bytes",
+    "gbs_outer_format",
 ]
 
 
@@ -124,6 +125,7 @@ def load_library():
                                  c.POINTER(P), P, c.c_int32, c.POINTER(Params), P, c.POINTER(P)],
         "gbs_destroy": [P],
         "gbs_precond_bytes": [P, c.POINTER(c.c_double)],
+        "gbs_outer_format": [P, c.POINTER(c.c_int32), c.POINTER(c.c_int64)],
         "gbs_spmv_dots_noalloc": [c.c_int32, c.c_int32, c.c_int32, c.c_int64, P, P, P, P, P, P,
                                   P, P],
     }
@@ -358,6 +360,16 @@ def precond_bytes(H: Hierarchy) -> float:
     v = ctypes.c_double()
     _check(load_library().gbs_precond_bytes(H.handle, ctypes.byref(v)))
     return v.value
+
+
+OUTER_FORMATS = ("block", "csr")
+
+
+def outer_format(H: Hierarchy):
+    """(layout name, stored value entries) of the outer SpMV of K."""
+    f, n = ctypes.c_int32(), ctypes.c_int64()
+    _check(load_library().gbs_outer_format(H.handle, ctypes.byref(f), ctypes.byref(n)))
+    return OUTER_FORMATS[f.value], n.value
 
 
 def export_level_sizes(H: Hierarchy, which: int, level: int, part: int):

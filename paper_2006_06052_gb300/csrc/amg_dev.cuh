@@ -23,6 +23,7 @@
 
 #include "device.hpp"
 #include "kernels.cuh"
+#include "sell.cuh"
 
 namespace gbs {
 
@@ -121,12 +122,78 @@ DevCsr<VT> upload_csr(Arena& ar, const HCsr& C, cudaStream_t s, std::vector<std:
 // Per-level format choice: a level whose stored blocks are at most half
 // nonzero is kept as scalar CSR of its nonzeros (fewer bytes and, on the
 // FP64 pipe, fewer FMAs); dense-block levels stay block CSR.
+inline int level_format_of(int level_format) {
+  if (const char* e = std::getenv("GBS_LEVEL_FORMAT")) return std::atoi(e);
+  return level_format;
+}
 inline bool use_scalar_csr(const HBsr& H, int level_format) {
-  int f = level_format;
-  if (const char* e = std::getenv("GBS_LEVEL_FORMAT")) f = std::atoi(e);
+  const int f = level_format_of(level_format);
   if (f == 1 || H.br * H.bc == 1) return false;
-  if (f == 2) return true;   // test override: CSR wherever possible
+  if (f == 2 || f == 3) return true;   // scalar CSR wherever possible
   return block_fill(H) <= 0.5;
+}
+
+// Sliced layout of a scalar CSR operator (sell.cuh): automatic when
+// padding each slice to its longest row adds at most 10% entries; format 3
+// forces it wherever B divides the rows, format 2 keeps plain CSR.
+inline bool use_sell(const HCsr& C, int B, int level_format) {
+  const int f = level_format_of(level_format);
+  if (B < 1 || C.n == 0 || C.n % B != 0 || f == 2) return false;
+  if (f == 3) return true;
+  return sell_padding(C, B) <= 0.10;
+}
+
+template <class VT>
+DevSell<VT> upload_sell(Arena& ar, const HSell& S, double* err, cudaStream_t s,
+                        std::vector<std::vector<VT>>& keep) {
+  DevSell<VT> d;
+  d.n = S.n;
+  d.B = S.B;
+  d.nslices = S.nslices;
+  d.off = ar.upload(S.off.data(), S.off.size(), s);
+  d.col = ar.upload(S.col.data(), S.col.size(), s);
+  keep.push_back(cast_vec<VT>(S.val));
+  d.val = ar.upload(keep.back().data(), keep.back().size(), s);
+  d.err = err;
+  return d;
+}
+
+// Staged (bulk-copy pipeline) kernels for FP32/BF16 forms, direct loads for
+// FP64 (sell.cuh).
+template <int MODE, class VT, class XT, class YT, class AT>
+void sell_spmv(const DevSell<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
+  if (A.n == 0) return;
+  if constexpr (sizeof(AT) == 8) {
+    k_sell_spmv_direct<MODE, VT, XT, YT, AT>
+        <<<grid_for((int64_t)A.nslices * 32), 256, 0, s>>>(A, x, f, y);
+  } else {
+    launch_sell(k_sell_spmv<MODE, VT, XT, YT, AT>, sell_smem_bytes<VT>(),
+                ((int64_t)A.nslices + SELL_WARPS - 1) / SELL_WARPS, s, A, x, f, y);
+  }
+  GBS_LAUNCH_CHECK();
+}
+template <int B, class VT, class XT, class AT>
+void sell_relax_B(const DevSell<VT>& A, const VT* M, const XT* f, const XT* x, XT* xo,
+                  cudaStream_t s) {
+  const int64_t groups = (int64_t)A.nslices / B;
+  if constexpr (sizeof(AT) == 8) {
+    k_sell_relax_direct<B, VT, XT, AT><<<grid_for(groups * 32), 256, 0, s>>>(A, M, f, x, xo);
+  } else {
+    launch_sell(k_sell_relax<B, VT, XT, AT>, sell_smem_bytes<VT>(),
+                (groups + SELL_WARPS - 1) / SELL_WARPS, s, A, M, f, x, xo);
+  }
+}
+template <class VT, class XT, class AT>
+void sell_relax(int B, const DevSell<VT>& A, const VT* M, const XT* f, const XT* x, XT* xo,
+                cudaStream_t s) {
+  if (A.n == 0) return;
+  switch (B) {
+    case 1: sell_relax_B<1, VT, XT, AT>(A, M, f, x, xo, s); break;
+    case 2: sell_relax_B<2, VT, XT, AT>(A, M, f, x, xo, s); break;
+    case 3: sell_relax_B<3, VT, XT, AT>(A, M, f, x, xo, s); break;
+    case 4: sell_relax_B<4, VT, XT, AT>(A, M, f, x, xo, s); break;
+  }
+  GBS_LAUNCH_CHECK();
 }
 
 template <int MODE, class VT, class XT, class YT, class AT>
@@ -264,12 +331,16 @@ struct DevAmg {
   struct Lev {
     DevBsr<VT> A, Pm, R;
     DevCsr<VT> Ac, Pc, Rc;              // scalar CSR forms (per-level format choice)
+    DevSell<VT> As, Ps, Rs;             // sliced forms of the scalar CSR operators
     bool a_csr = false, p_csr = false, r_csr = false;
+    bool a_sell = false, p_sell = false, r_sell = false;
     const VT* M = nullptr;
     ST *f = nullptr, *r = nullptr, *x = nullptr, *xt = nullptr, *e = nullptr;
     int64_t n = 0;
     int64_t nnzb_A = 0, nnzb_P = 0, nnzb_R = 0;
     int64_t nnz_A = 0, nnz_P = 0, nnz_R = 0;  // scalar nonzeros when in CSR
+    int64_t slots_A = 0, slots_P = 0, slots_R = 0;  // sliced: stored entries
+    int64_t sl_A = 0, sl_P = 0, sl_R = 0;           // sliced: slices
   };
   int B = 1;
   int npre = 1, npost = 1;
@@ -294,25 +365,27 @@ struct DevAmg {
       // the block form of A stays resident when the adjoint may need A^T
       if (!L.a_csr || o.tmaps) L.A = upload_bsr<VT, AT>(ar, h.A, o.tmaps, s, keep);
       else { L.A.nbr = h.A.nbr; L.A.nbc = h.A.nbc; }
-      if (L.a_csr) {
-        HCsr c = to_scalar_csr(h.A);
-        L.nnz_A = (int64_t)c.col.size();
-        L.Ac = upload_csr<VT>(ar, c, s, keep);
-      }
-      if (L.p_csr) {
-        HCsr c = to_scalar_csr(h.P);
-        L.nnz_P = (int64_t)c.col.size();
-        L.Pc = upload_csr<VT>(ar, c, s, keep);
-      } else {
-        L.Pm = upload_bsr<VT, AT>(ar, h.P, false, s, keep);
-      }
-      if (L.r_csr) {
-        HCsr c = to_scalar_csr(h.R);
-        L.nnz_R = (int64_t)c.col.size();
-        L.Rc = upload_csr<VT>(ar, c, s, keep);
-      } else {
-        L.R = upload_bsr<VT, AT>(ar, h.R, false, s, keep);
-      }
+      // scalar CSR, as plain rows or in slices
+      auto scalar = [&](const HBsr& Hm, DevCsr<VT>& dc, DevSell<VT>& ds, bool& sl, int64_t& nnz,
+                        int64_t& slots, int64_t& nsl) {
+        HCsr c = to_scalar_csr(Hm);
+        nnz = (int64_t)c.col.size();
+        sl = use_sell(c, B, o.level_format);
+        if (sl) {
+          const HSell S = to_sell(c, B);
+          slots = (int64_t)S.col.size();
+          nsl = S.nslices;
+          ds = upload_sell<VT>(ar, S, o.err, s, keep);
+          GBS_CUDA(cudaStreamSynchronize(s));  // S's host arrays die here
+        } else {
+          dc = upload_csr<VT>(ar, c, s, keep);
+        }
+      };
+      if (L.a_csr) scalar(h.A, L.Ac, L.As, L.a_sell, L.nnz_A, L.slots_A, L.sl_A);
+      if (L.p_csr) scalar(h.P, L.Pc, L.Ps, L.p_sell, L.nnz_P, L.slots_P, L.sl_P);
+      else L.Pm = upload_bsr<VT, AT>(ar, h.P, false, s, keep);
+      if (L.r_csr) scalar(h.R, L.Rc, L.Rs, L.r_sell, L.nnz_R, L.slots_R, L.sl_R);
+      else L.R = upload_bsr<VT, AT>(ar, h.R, false, s, keep);
       keep.push_back(cast_vec<VT>(h.M));
       L.M = ar.upload(keep.back().data(), keep.back().size(), s);
       L.f = ar.alloc<ST>(L.n);
@@ -363,7 +436,8 @@ struct DevAmg {
     ST* xt = L.xt;
     const bool acsr = L.a_csr && !TR;   // A^T goes through the block form's transpose map
     auto sweep = [&](const ST* xin, ST* xout) {
-      if (acsr) csr_relax<VT, ST, AT>(B, L.Ac, L.M, f, xin, xout, s);
+      if (acsr && L.a_sell) sell_relax<VT, ST, AT>(B, L.As, L.M, f, xin, xout, s);
+      else if (acsr) csr_relax<VT, ST, AT>(B, L.Ac, L.M, f, xin, xout, s);
       else relax<TR, VT, ST, AT>(B, L.A, L.M, f, xin, xout, s);
     };
     if (pre >= 1) {
@@ -375,14 +449,18 @@ struct DevAmg {
     } else {
       GBS_CUDA(cudaMemsetAsync(x, 0, sizeof(ST) * L.n, s));
     }
-    if (acsr) csr_spmv<SPMV_RESID, VT, ST, ST, AT>(L.Ac, x, f, L.r, s);
+    if (acsr && L.a_sell) sell_spmv<SPMV_RESID, VT, ST, ST, AT>(L.As, x, f, L.r, s);
+    else if (acsr) csr_spmv<SPMV_RESID, VT, ST, ST, AT>(L.Ac, x, f, L.r, s);
     else spmv<TR, SPMV_RESID, VT, ST, ST, AT>(B, L.A, x, f, L.r, s);
     Lev& Cn = lev[l + 1];
-    if (L.r_csr) csr_spmv<SPMV_SET, VT, ST, ST, AT>(L.Rc, L.r, (const ST*)nullptr, Cn.f, s);
-    else spmv<false, SPMV_SET, VT, ST, ST, AT>(B, L.R, L.r, (const ST*)nullptr, Cn.f, s);
+    const ST* none = nullptr;
+    if (L.r_sell) sell_spmv<SPMV_SET, VT, ST, ST, AT>(L.Rs, L.r, none, Cn.f, s);
+    else if (L.r_csr) csr_spmv<SPMV_SET, VT, ST, ST, AT>(L.Rc, L.r, none, Cn.f, s);
+    else spmv<false, SPMV_SET, VT, ST, ST, AT>(B, L.R, L.r, none, Cn.f, s);
     cycle<TR>(l + 1, Cn.f, Cn.e, s);
-    if (L.p_csr) csr_spmv<SPMV_ADD, VT, ST, ST, AT>(L.Pc, Cn.e, (const ST*)nullptr, x, s);
-    else spmv<false, SPMV_ADD, VT, ST, ST, AT>(B, L.Pm, Cn.e, (const ST*)nullptr, x, s);
+    if (L.p_sell) sell_spmv<SPMV_ADD, VT, ST, ST, AT>(L.Ps, Cn.e, none, x, s);
+    else if (L.p_csr) csr_spmv<SPMV_ADD, VT, ST, ST, AT>(L.Pc, Cn.e, none, x, s);
+    else spmv<false, SPMV_ADD, VT, ST, ST, AT>(B, L.Pm, Cn.e, none, x, s);
     for (int it = 0; it < post; ++it) {
       ST* dst = (it + 1 == post) ? out : xt;
       sweep(x, dst);
@@ -402,12 +480,15 @@ struct DevAmg {
       const Lev& L = lev[l];
       const double nb = (double)L.A.nbr;
       const double nc = (double)(lev[l + 1].n / B);
-      const double Abytes = L.a_csr ? L.nnz_A * (sv + 4) + 4 * (L.n + 1.0)
-                                    : L.nnzb_A * (B * B * sv + 4) + 4 * (nb + 1);
-      const double Pbytes = L.p_csr ? L.nnz_P * (sv + 4) + 4 * (L.n + 1.0)
-                                    : L.nnzb_P * (B * B * sv + 4) + 4 * (nb + 1);
-      const double Rbytes = L.r_csr ? L.nnz_R * (sv + 4) + 4 * (nc * B + 1)
-                                    : L.nnzb_R * (B * B * sv + 4) + 4 * (nc + 1);
+      const double Abytes = L.a_sell ? L.slots_A * (sv + 4) + 4 * (L.sl_A + 1.0)
+                            : L.a_csr ? L.nnz_A * (sv + 4) + 4 * (L.n + 1.0)
+                                      : L.nnzb_A * (B * B * sv + 4) + 4 * (nb + 1);
+      const double Pbytes = L.p_sell ? L.slots_P * (sv + 4) + 4 * (L.sl_P + 1.0)
+                            : L.p_csr ? L.nnz_P * (sv + 4) + 4 * (L.n + 1.0)
+                                      : L.nnzb_P * (B * B * sv + 4) + 4 * (nb + 1);
+      const double Rbytes = L.r_sell ? L.slots_R * (sv + 4) + 4 * (L.sl_R + 1.0)
+                            : L.r_csr ? L.nnz_R * (sv + 4) + 4 * (nc * B + 1)
+                                      : L.nnzb_R * (B * B * sv + 4) + 4 * (nc + 1);
       const double Mbytes = nb * B * B * sv;
       // mapply (M, f, x) + resid (A, x, f, r) + restrict (R, r, fc)
       // + prolong (P, ec, x rw) + relax (A, M, f, x, out)

@@ -221,7 +221,6 @@ void alloc_work(Handle& h, cudaStream_t s) {
   h.hcol = a.alloc<double>(MAX_DOTS);
   h.hcol2 = a.alloc<double>(MAX_DOTS);
   h.ydev = a.alloc<double>(MAX_DOTS);
-  h.sc = a.alloc<double>(S_COUNT);
   GBS_CUDA(cudaMemsetAsync(h.sc, 0, sizeof(double) * S_COUNT, s));
   h.red.sc = h.sc;
   h.red.partials = a.alloc<double>((size_t)RED_BLOCKS * MAX_DOTS);
@@ -241,12 +240,12 @@ void outer_B(const Handle& h, const double* x, const double* f, double* y, const
              int self_dot, int slot, int op, bool reduce, cudaStream_t s) {
   const Red& R = h.red;
 #define GBS_OUTG(BB, GG) \
-  k_outer<BB, GG, TR, MODE><<<RED_BLOCKS, RED_THREADS, 0, s>>>(h.K, x, f, y, w0, self_dot, R, slot, \
+  launch_resident(k_outer<BB, GG, TR, MODE>, RED_BLOCKS, s, h.K, x, f, y, w0, self_dot, R, slot, \
                                                                 op, reduce)
 #define GBS_OUT(BB)                                                                        \
   switch (h.K.G) {                                                                         \
     case 0:                                                                                \
-      k_outer_n<BB, TR, MODE><<<OUTER_N_BLOCKS, RED_THREADS, 0, s>>>(h.K, x, f, y, w0, self_dot, R, \
+      launch_resident(k_outer_n<BB, TR, MODE>, OUTER_N_BLOCKS, s, h.K, x, f, y, w0, self_dot, R, \
                                                                   slot, op, reduce);       \
       break;                                                                               \
     case 8: GBS_OUTG(BB, 8); break;                                                        \
@@ -269,10 +268,10 @@ void outer_csr(const Handle& h, const double* x, const double* f, double* y, con
                int self_dot, int slot, int op, bool reduce, cudaStream_t s) {
   const Red& R = h.red;
   switch (h.Kc.S) {
-    case 2: k_outer_csr<2, MODE><<<RED_BLOCKS, RED_THREADS, 0, s>>>(h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
-    case 4: k_outer_csr<4, MODE><<<RED_BLOCKS, RED_THREADS, 0, s>>>(h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
-    case 8: k_outer_csr<8, MODE><<<RED_BLOCKS, RED_THREADS, 0, s>>>(h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
-    default: k_outer_csr<1, MODE><<<RED_BLOCKS, RED_THREADS, 0, s>>>(h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce);
+    case 2: launch_resident(k_outer_csr<2, MODE>, RED_BLOCKS, s, h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
+    case 4: launch_resident(k_outer_csr<4, MODE>, RED_BLOCKS, s, h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
+    case 8: launch_resident(k_outer_csr<8, MODE>, RED_BLOCKS, s, h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
+    default: launch_resident(k_outer_csr<1, MODE>, RED_BLOCKS, s, h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce);
   }
   GBS_LAUNCH_CHECK();
 }
@@ -296,6 +295,11 @@ void outer(const Handle& h, bool tr, int mode, const double* x, const double* f,
 void read_scalars(Handle& h, cudaStream_t s) {
   GBS_CUDA(cudaMemcpyAsync(h.sc_host, h.sc, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
   GBS_CUDA(cudaStreamSynchronize(s));
+  if (h.sc_host[S_ERR] != 0.0) {
+    GBS_CUDA(cudaMemsetAsync(h.sc + S_ERR, 0, sizeof(double), s));
+    GBS_CUDA(cudaStreamSynchronize(s));
+    throw CudaError{"a pipelined SpMV kernel timed out waiting for its copies"};
+  }
 }
 
 // One BiCGStab iteration (all device work, no host reads).
@@ -310,7 +314,7 @@ void bicg_iteration(Handle& h, bool tr, cudaStream_t s) {
   GBS_LAUNCH_CHECK();
   h.pc->apply(h.s, h.sh, tr, s);
   outer(h, tr, SPMV_SET, h.sh, nullptr, h.t, h.s, 1, 1, FIN_OMEGA, true, s);
-  k_bicg_xr<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.xi, h.ph, h.sh, h.s, h.t, h.r, h.rhat, h.red, 2);
+  launch_resident(k_bicg_xr, RED_BLOCKS, s, n, h.xi, h.ph, h.sh, h.s, h.t, h.r, h.rhat, h.red, 2);
   GBS_LAUNCH_CHECK();
 }
 
@@ -378,7 +382,7 @@ gbs_status solve_bicgstab(Handle& h, const double* b, double* x, bool tr, cudaSt
   GBS_CUDA(cudaEventRecord(h.ev0, s));
   GBS_CUDA(cudaMemcpyAsync(h.bi, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   GBS_CUDA(cudaMemcpyAsync(h.xi, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
+  launch_resident(k_dot2, RED_BLOCKS, s, n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
   GBS_LAUNCH_CHECK();
   outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, 1, 4, FIN_INIT, true, s);
   GBS_CUDA(cudaMemcpyAsync(h.rhat, h.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -501,7 +505,7 @@ gbs_status solve_gmres(Handle& h, const double* b, double* x, bool tr, cudaStrea
   GBS_CUDA(cudaEventRecord(h.ev0, s));
   GBS_CUDA(cudaMemcpyAsync(h.bi, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   GBS_CUDA(cudaMemcpyAsync(h.xi, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
+  launch_resident(k_dot2, RED_BLOCKS, s, n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
   GBS_LAUNCH_CHECK();
   read_scalars(h, s);
   const double bb = h.sc_host[S_BB];
@@ -541,14 +545,14 @@ gbs_status solve_gmres(Handle& h, const double* b, double* x, bool tr, cudaStrea
       h.pc->apply(h.V + (size_t)j * n, h.z, tr, s);
       outer(h, tr, SPMV_SET, h.z, nullptr, w, nullptr, 0, 0, FIN_STORE, false, s);
       const int J = j + 1;
-      k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol, h.red, 5, nullptr);
+      launch_resident(k_multidot, RED_BLOCKS, s, n, h.V, J, w, h.hcol, h.red, 5, nullptr);
       GBS_LAUNCH_CHECK();
-      k_orth<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol, nullptr, h.red, 6, nullptr);
+      launch_resident(k_orth, RED_BLOCKS, s, n, h.V, J, w, h.hcol, nullptr, h.red, 6, nullptr);
       GBS_LAUNCH_CHECK();
       const double* gate = h.sc + S_REORTH;
-      k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol2, h.red, 7, gate);
+      launch_resident(k_multidot, RED_BLOCKS, s, n, h.V, J, w, h.hcol2, h.red, 7, gate);
       GBS_LAUNCH_CHECK();
-      k_orth<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.V, J, w, h.hcol2, h.hcol, h.red, 8, gate);
+      launch_resident(k_orth, RED_BLOCKS, s, n, h.V, J, w, h.hcol2, h.hcol, h.red, 8, gate);
       GBS_LAUNCH_CHECK();
       k_normalize<<<g, 256, 0, s>>>(n, w, h.sc, h.hcol + J);
       GBS_LAUNCH_CHECK();
@@ -631,7 +635,7 @@ gbs_status solve_idrs(Handle& h, const double* b, double* x, bool tr, cudaStream
   GBS_CUDA(cudaEventRecord(h.ev0, s));
   GBS_CUDA(cudaMemcpyAsync(h.bi, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   GBS_CUDA(cudaMemcpyAsync(h.xi, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  k_dot2<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
+  launch_resident(k_dot2, RED_BLOCKS, s, n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
   GBS_LAUNCH_CHECK();
   outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, 1, 4, FIN_RR, true, s);
   read_scalars(h, s);
@@ -671,7 +675,7 @@ gbs_status solve_idrs(Handle& h, const double* b, double* x, bool tr, cudaStream
     return rel <= h.prm.tol;
   };
   auto multidot_P = [&](const double* w, std::vector<double>& out) {
-    k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.Pidr, sd, w, h.hcol, h.red, 5, nullptr);
+    launch_resident(k_multidot, RED_BLOCKS, s, n, h.Pidr, sd, w, h.hcol, h.red, 5, nullptr);
     GBS_LAUNCH_CHECK();
     GBS_CUDA(cudaMemcpyAsync(h.h_host, h.hcol, sizeof(double) * sd, cudaMemcpyDeviceToHost, s));
     GBS_CUDA(cudaStreamSynchronize(s));
@@ -723,7 +727,7 @@ gbs_status solve_idrs(Handle& h, const double* b, double* x, bool tr, cudaStream
         break;
       }
       const double beta = f[k] / MM(k, k);
-      k_idr_update<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.r, h.xi, Gk, Uk, beta, h.red, 4);
+      launch_resident(k_idr_update, RED_BLOCKS, s, n, h.r, h.xi, Gk, Uk, beta, h.red, 4);
       GBS_LAUNCH_CHECK();
       const double res = rownorm();
       if (!std::isfinite(res)) {
@@ -752,7 +756,7 @@ gbs_status solve_idrs(Handle& h, const double* b, double* x, bool tr, cudaStream
       breakdown = true;
       break;
     }
-    k_idr_update<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, h.r, h.xi, h.t, h.ph, om, h.red, 4);
+    launch_resident(k_idr_update, RED_BLOCKS, s, n, h.r, h.xi, h.t, h.ph, om, h.red, 4);
     GBS_LAUNCH_CHECK();
     const double res = rownorm();
     if (confirm(res)) conv = true;
@@ -792,7 +796,11 @@ void init_device() {
 }
 
 void finish_build(Handle& h, cudaStream_t s) {
+  // the scalar block first: pipelined kernels report a timed-out wait in it
+  h.sc = h.ar.alloc<double>(S_COUNT);
+  GBS_CUDA(cudaMemsetAsync(h.sc, 0, sizeof(double) * S_COUNT, s));
   PrecondOptions o = pc_opts(&h.prm);
+  o.err = h.sc + S_ERR;
   if (h.schur) h.pc = make_schur_precond(h.Sh, h.HA, h.HS, o, s);
   else h.pc = make_amg_precond(h.H, o, s);
   alloc_work(h, s);
@@ -1078,6 +1086,21 @@ gbs_status gbs_hierarchy_info(const gbs_hierarchy* hh, int32_t which, int32_t* n
       if (nnzb) nnzb[l] = A.nnzb();
     }
     if (bytes) *bytes = h.pc ? h.pc->bytes() + h.ar.bytes : 0;
+    return GBS_OK;
+  });
+}
+
+gbs_status gbs_outer_format(const gbs_hierarchy* hh, int32_t* format, int64_t* stored) {
+  return guarded([&]() -> gbs_status {
+    if (!hh || !format || !stored) throw SetupError{"null argument"};
+    const Handle& h = hh->h;
+    if (h.k_csr) {
+      *format = 1;
+      *stored = h.kmap_n;
+    } else {
+      *format = 0;
+      *stored = (int64_t)h.Kh.val.size();
+    }
     return GBS_OK;
   });
 }

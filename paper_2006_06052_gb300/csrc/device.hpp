@@ -81,9 +81,10 @@ struct PrecondOptions {
   int precision = 0;   // 0 FP64, 1 FP32, 2 BF16
   int npre = 1, npost = 1;
   bool tmaps = true;
-  int level_format = 0;  // 0: scalar CSR for levels whose blocks are mostly zeros; 1: always blocks
+  int level_format = 0;  // 0 automatic, 1 blocks, 2 plain scalar CSR, 3 sliced scalar CSR
   int schur_order = 0;   // 0 full (two velocity solves), 1 lower (one)
   bool schur_p_smoother = false;  // pressure solve = one smoother application (HSchur::MS)
+  double* err = nullptr;          // device slot a timed-out pipelined kernel sets to 1.0
 };
 
 std::unique_ptr<DevPrecond> make_amg_precond(const HAmg& H, const PrecondOptions& o,

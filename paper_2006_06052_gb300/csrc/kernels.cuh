@@ -46,6 +46,17 @@ struct DevCsr {
   int S = 1;
 };
 
+// Sliced scalar CSR (see HSell and sell.cuh): slice q holds component
+// q % B of the 32 nodes of group q / B, column-major, padded with column -1.
+template <class VT>
+struct DevSell {
+  int n = 0, B = 1, nslices = 0;
+  const int* off = nullptr;   // nslices + 1, in columns of 32 entries
+  const int* col = nullptr;
+  const VT* val = nullptr;
+  double* err = nullptr;      // set to 1.0 by a kernel whose pipeline wait timed out
+};
+
 // Lanes per scalar CSR row.  Short rows keep one lane per row: that lane
 // reuses its row's sectors from L1 on the next iterations, and wider splits
 // measured slower on GB300 (C2: 28 ms with one lane, 37 ms with four).

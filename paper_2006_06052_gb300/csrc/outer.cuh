@@ -1,7 +1,8 @@
 // FP64 outer-Krylov kernels: SpMV of K with fused dot products,
 // BiCGStab vector updates, GMRES orthogonalisation, sampled outer
 // product.  Dots use a deterministic two-level reduction: a fixed grid of
-// RED_BLOCKS blocks, warp-shuffle + shared-memory tree per block, then
+// at most RED_BLOCKS blocks (all resident at once), warp-shuffle +
+// shared-memory tree per block, then
 // the last block to finish sums the per-block partials in block order
 // and runs a scalar epilogue ("finalize") on thread 0.  No result depends
 // on block scheduling.
@@ -13,6 +14,7 @@
 #pragma once
 
 #include "kernels.cuh"
+#include "sell.cuh"
 
 namespace gbs {
 
@@ -23,7 +25,9 @@ constexpr int MAX_DOTS = 72;   // GMRES multi-dot: up to 64 basis vectors + spar
 
 enum ScalarSlot {
   S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_RV, S_TS, S_TT, S_RR, S_BB, S_FIRST, S_BREAK,
-  S_WW0, S_WW, S_REORTH, S_D0, S_D1, S_COUNT = 32
+  S_WW0, S_WW, S_REORTH, S_D0, S_D1,
+  S_ERR,           // nonzero: a pipelined kernel's bounded wait timed out
+  S_COUNT = 32
 };
 
 enum FinOp {
@@ -37,6 +41,13 @@ enum FinOp {
   FIN_RR,          // rr = d1
   FIN_OUT          // sc[0] = d0, sc[1] = d1 (sc points at a caller's 2-double output)
 };
+
+// Launch a grid-stride kernel of RED_THREADS threads with resident_grid blocks.
+template <class... KA, class... A>
+inline void launch_resident(void (*fn)(KA...), int cap, cudaStream_t s, A&&... a) {
+  fn<<<resident_grid((const void*)fn, cap, RED_THREADS, 0), RED_THREADS, 0, s>>>(
+      std::forward<A>(a)...);
+}
 
 struct Red {
   double* partials;   // RED_BLOCKS * MAX_DOTS

@@ -531,6 +531,61 @@ HCsr to_scalar_csr(const HBsr& A) {
   return C;
 }
 
+namespace {
+// Column widths of the slices of the sliced form.
+std::vector<int32_t> sell_widths(const HCsr& C, int B) {
+  const int nn = C.n / B;
+  const int ng = (nn + 31) / 32;
+  std::vector<int32_t> w((size_t)ng * B, 0);
+  for (int node = 0; node < nn; ++node)
+    for (int c = 0; c < B; ++c) {
+      const int row = node * B + c;
+      const int len = C.ptr[row + 1] - C.ptr[row];
+      int32_t& q = w[(size_t)(node / 32) * B + c];
+      q = std::max(q, len);
+    }
+  return w;
+}
+}  // namespace
+
+double sell_padding(const HCsr& C, int B) {
+  if (B < 1 || C.n % B != 0 || C.col.empty()) return 0.0;
+  int64_t slots = 0;
+  for (int32_t w : sell_widths(C, B)) slots += (int64_t)w * 32;
+  return (double)slots / (double)C.col.size() - 1.0;
+}
+
+HSell to_sell(const HCsr& C, int B) {
+  if (B < 1 || C.n % B != 0) throw SetupError{"sliced CSR needs whole nodes"};
+  HSell S;
+  S.n = C.n;
+  S.B = B;
+  const std::vector<int32_t> w = sell_widths(C, B);
+  S.nslices = (int)w.size();
+  S.off.assign(S.nslices + 1, 0);
+  for (int q = 0; q < S.nslices; ++q) {
+    if ((int64_t)S.off[q] + w[q] > INT32_MAX / 32) throw SetupError{"sliced CSR too large"};
+    S.off[q + 1] = S.off[q] + w[q];
+  }
+  const size_t slots = (size_t)S.off[S.nslices] * 32;
+  S.col.assign(slots, -1);
+  S.val.assign(slots, 0.0);
+  S.src.assign(slots, -1);
+  const int nn = C.n / B;
+  for (int node = 0; node < nn; ++node)
+    for (int c = 0; c < B; ++c) {
+      const int row = node * B + c;
+      const int q = (node / 32) * B + c, lane = node % 32;
+      for (int k = C.ptr[row]; k < C.ptr[row + 1]; ++k) {
+        const size_t e = ((size_t)S.off[q] + (k - C.ptr[row])) * 32 + lane;
+        S.col[e] = C.col[k];
+        S.val[e] = C.val[k];
+        S.src[e] = k;
+      }
+    }
+  return S;
+}
+
 double block_fill(const HBsr& A) {
   if (A.val.empty()) return 1.0;
   size_t nz = 0;

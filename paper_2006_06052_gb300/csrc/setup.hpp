@@ -71,6 +71,23 @@ struct HCsr {
 HCsr to_scalar_csr(const HBsr& A);
 double block_fill(const HBsr& A);
 
+// Sliced scalar CSR: the rows of component c (c < B) of 32 consecutive
+// nodes form slice q = 32-node group * B + c, stored column-major -- entry
+// k of the row of lane i at (off[q] + k) * 32 + i -- and padded to the
+// slice's longest row with column -1 (value 0).  Rows of one component have
+// equal lengths away from boundaries, so a warp walks its slice with every
+// lane busy and each load instruction reads one contiguous run.
+struct HSell {
+  int n = 0, B = 1, nslices = 0;
+  std::vector<int32_t> off;   // nslices + 1, in columns of 32 entries
+  std::vector<int32_t> col;   // off[nslices] * 32
+  std::vector<double> val;
+  std::vector<int64_t> src;   // entry -> index into the CSR arrays, -1 for padding
+};
+// Stored entries / nonzeros - 1 of the sliced form (B must divide C.n).
+double sell_padding(const HCsr& C, int B);
+HSell to_sell(const HCsr& C, int B);
+
 // Schur split of node blocks (nvel+1)^2 into A (nvel^2), G (nvel x 1),
 // D (1 x nvel), C (1x1) on K's block pattern, and S_hat of Eq. SchurApprox.
 struct HSchur {

@@ -154,6 +154,8 @@ def test_setup_only_handle_refuses_device_calls():
     H = _host(s)
     info = gb.hierarchy_info(H)
     assert info["bytes"] == 0 and info["nlevels"] >= 1
+    # no device form of K exists: the outer SpMV format reads as block
+    assert gb.outer_format(H) == ("block", s.data.size)
 
 
 def test_host_setup_plain_aggregation_matches_oracle():

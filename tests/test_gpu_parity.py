@@ -52,8 +52,12 @@ def check_spmv(H, A, x, transpose=False):
 
 
 # ------------------------------------------------------------------ SpMV
+@pytest.mark.parametrize("fmt", ["0", "1", "2"])
 @pytest.mark.parametrize("case", ["c1_csr", "c2_bsr4", "vel_bsr3"])
-def test_outer_spmv_and_transpose(case):
+def test_outer_spmv_and_transpose(case, fmt, monkeypatch):
+    """K in block form (1), as scalar CSR of its nonzeros (2), or as chosen
+    automatically (0)."""
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
     N = 9   # 729 nodes: a ragged tail for every rows-per-warp grouping
     if case == "c1_csr":
         s = si.make_system("c1", N=N)
@@ -96,11 +100,12 @@ def _import(Ho, B, **kw):
     return gb.import_hierarchy(As, Ps, Rs, Ms, Ho.Ainv_coarse, B, gb.params_default(**kw))
 
 
-@pytest.mark.parametrize("fmt", ["0", "1", "2"])
+@pytest.mark.parametrize("fmt", ["0", "1", "2", "3"])
 @pytest.mark.parametrize("cfg", [("c2", 9, "jacobi"), ("c2", 10, "spai0"), ("c1", 9, "spai0")])
 def test_vcycle_on_imported_oracle_hierarchy(cfg, fmt, monkeypatch):
-    """Level formats: 0 automatic (scalar CSR where blocks are mostly zero),
-    1 block CSR everywhere, 2 scalar CSR wherever possible."""
+    """Level formats: 0 automatic (scalar CSR where blocks are mostly zero,
+    sliced where that pads little), 1 block CSR everywhere, 2 plain scalar
+    CSR wherever possible, 3 sliced scalar CSR wherever possible."""
     monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
     name, N, relax = cfg
     s = si.make_system(name, N=N)
@@ -167,7 +172,7 @@ def test_schur_apply_matches_oracle():
         assert rel_inf(z, ref) <= 1e-10, (tr, rel_inf(z, ref))
 
 
-@pytest.mark.parametrize("fmt", ["1", "2"])
+@pytest.mark.parametrize("fmt", ["1", "2", "3"])
 @pytest.mark.parametrize("S", ["1", "2", "4", "8"])
 def test_schur_apply_every_row_split(S, fmt, monkeypatch):
     """3x3 velocity and scalar pressure hierarchies with each row split, in
@@ -188,17 +193,19 @@ def test_schur_apply_every_row_split(S, fmt, monkeypatch):
         assert rel_inf(z, pc.apply(r, transpose=tr)) <= 1e-10
 
 
+@pytest.mark.parametrize("fmt", ["2", "3"])
 @pytest.mark.parametrize("S", ["1", "4"])
 @pytest.mark.parametrize("precision", [gb.GBS_FP32, gb.GBS_BF16])
-def test_mixed_csr_levels_match_block_levels(precision, S, monkeypatch):
-    """The scalar CSR form of a mixed-precision level computes the same
-    operator as its block form (FP32 accumulation: 1e-5 relative)."""
+def test_mixed_csr_levels_match_block_levels(precision, S, fmt, monkeypatch):
+    """The scalar CSR form (plain or sliced) of a mixed-precision level
+    computes the same operator as its block form (FP32 accumulation: 1e-5
+    relative)."""
     monkeypatch.setenv("GBS_SPMV_SPLIT", S)
     s = si.make_system("c3", N=10)
     p = _params(s, precision=precision, coarse_enough=60)
     monkeypatch.setenv("GBS_LEVEL_FORMAT", "1")
     Hb = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, p)
-    monkeypatch.setenv("GBS_LEVEL_FORMAT", "2")
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
     Hc = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, p)
     r = dev(np.random.default_rng(9).standard_normal(s.n))
     zb = host(gb.apply_precond(Hb, r))
@@ -430,11 +437,13 @@ def test_full_size_c4_adjoint_central_differences():
     """C4 at full size (N=64, 4x4 BSR FP64): L = 1/2 ||x - x_t||^2, adjoint
     gradient of 64 random stored entries (seed 4002) against FP64 central
     differences (h = 1e-6) with solves to 1e-13 reusing the hierarchy.
-    Tolerance: 5e-5 relative per entry, with entries below 1% of max|G|
-    compared at 5e-7 max|G|.  The difference quotient carries the error of
-    two 1e-13 solves (cond(K) ~ 1e4 at N=64) divided by the step; at full
-    size it reaches ~2e-5 relative on some entries, above the 1e-5 the
-    small-grid checks use."""
+    Tolerance per entry: 5e-5 relative, or 1e-5 max|G| absolute, whichever
+    is larger.  The absolute term is the difference quotient's noise: each
+    solve stops at relative residual 1e-13, leaving an error of order
+    cond(K) 1e-13 |x| (cond(K) ~ 1e4 at N=64) that does not cancel exactly
+    between the two solves, and that error is divided by the step (seen up
+    to 1.6e-6 max|G|).  A wrong gradient is off by O(1) on entries of any
+    size; the small-grid tests pin it to 1e-5 and to the dense inverse."""
     from paper_2006_06052_gb300.autograd import stokes_solve
     s = si.make_system("c4")
     xt = dev(si.gaussian_vector(s.n, 4001))
@@ -460,7 +469,7 @@ def test_full_size_c4_adjoint_central_differences():
             xp = stokes_solve(vp, dev(s.b), H)
             xm = stokes_solve(vm, dev(s.b), H)
         fd = 0.5 * torch.dot(xp - xm, xp + xm - 2 * xt).item() / (2 * step)
-        assert abs(fd - G[idx]) <= 5e-5 * max(abs(fd), 1e-2 * gmax), (idx, fd, G[idx])
+        assert abs(fd - G[idx]) <= max(5e-5 * abs(fd), 1e-5 * gmax), (idx, fd, G[idx])
     # grad_b by central differences on a few unknowns
     for i in rng.integers(s.n, size=4):
         e = torch.zeros(s.n, dtype=torch.float64, device="cuda")
@@ -469,7 +478,7 @@ def test_full_size_c4_adjoint_central_differences():
             xp = stokes_solve(v0, dev(s.b) + e, H)
             xm = stokes_solve(v0, dev(s.b) - e, H)
         fd = 0.5 * torch.dot(xp - xm, xp + xm - 2 * xt).item() / 2e-6
-        assert abs(fd - gb_[int(i)]) <= 5e-5 * max(abs(fd), 1e-2 * np.abs(gb_).max())
+        assert abs(fd - gb_[int(i)]) <= max(5e-5 * abs(fd), 1e-5 * np.abs(gb_).max())
 
 
 @pytest.mark.parametrize("N", [24, pytest.param(128, id="full_size")])
@@ -494,6 +503,24 @@ def test_c5_mixed_adjoint_matches_fp64_adjoint(N):
     assert abs(n16 - n64) <= 1e-5 * n64
     assert np.linalg.norm(g16 - g64) <= 1e-4 * n64
     assert abs(grads[gb.GBS_BF16][1] - grads[gb.GBS_FP64][1]) <= 1e-4 * grads[gb.GBS_FP64][1]
+
+
+def test_update_values_inside_csr_pattern():
+    """New values on K's build-time nonzero pattern reach the scalar CSR
+    form of K."""
+    s = si.make_system("c2", N=7)
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, _params(s, relax=gb.GBS_JACOBI))
+    gb.solve(H, dev(s.b))
+    rng = np.random.default_rng(12)
+    vals = s.data * (1.0 + 0.25 * rng.random(s.data.shape))
+    K2 = bsr.from_arrays(s.indptr, s.indices, vals, 4).scipy()
+    gb.update_values(H, dev(vals.reshape(-1)))
+    x = rng.standard_normal(s.n)
+    y = host(gb.spmv(H, dev(x)))
+    assert np.all(np.abs(y - K2 @ x) <= 1e-13 * (abs(K2) @ np.abs(x)) + 1e-300)
+    xs, info = gb.solve(H, dev(s.b))
+    assert info.converged
+    assert np.linalg.norm(s.b - K2 @ host(xs)) / np.linalg.norm(s.b) <= 1e-8
 
 
 def test_update_values_outside_csr_pattern_falls_back_to_blocks():
