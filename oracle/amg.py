@@ -30,6 +30,9 @@ silent) are:
    scalar m_i = a_ii / sum_j a_ij^2; for blocks the minimiser of
    ||I - M A||_F over block-diagonal M, M_i = A_ii^T (sum_j A_ij A_ij^T)^-1.
    Damped Jacobi (PETSc's choice in Section 4) is M_i = omega A_ii^-1.
+   ILUT (the paper's velocity smoother, Listings V2-V4) is in ilut.py: there
+   the step x += S (f - A x) uses the approximate (LU)^-1 of that file in
+   place of the block-diagonal M.
 7. V-cycle: 1 pre-sweep from a zero guess (x = M f), residual,
    restriction, recursive coarse correction, prolongation, 1 post-sweep
    x += M (f - A x); the transposed cycle uses A^T, M^T, the same P and
@@ -42,6 +45,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.sparse as sp
 
+from . import ilut as ilut_mod
 from .bsr import Bsr, from_scipy, spmv
 
 
@@ -52,18 +56,23 @@ class AmgParams:
     max_levels: int = 10
     npre: int = 1
     npost: int = 1
-    relax: str = "spai0"             # "spai0" | "jacobi"
+    relax: str = "spai0"             # "spai0" | "jacobi" | "ilut"
     jacobi_omega: float = 0.72
     smooth_P: bool = True
+    ilut_p: float = 2.0              # ILUT fill factor (ilut.py reading 1)
+    ilut_tau: float = 1e-2           # ILUT drop tolerance
+    ilut_sweeps: int = 2             # Jacobi sweeps per triangular solve
+    ilut_omega: float = 1.0          # ILUT relaxation damping
 
 
 @dataclass
 class Level:
     A: Bsr
-    M: np.ndarray        # [n_brows, B, B] smoother blocks
+    M: np.ndarray        # [n_brows, B, B] smoother blocks (SPAI0 / Jacobi)
     P: Bsr               # n x n_c
     R: Bsr               # n_c x n
     agg: np.ndarray      # aggregate id of every block node
+    S: object = None     # ilut.Ilu when the level is relaxed by ILUT
 
 
 @dataclass
@@ -236,8 +245,17 @@ def build_hierarchy(A: Bsr, prm: AmgParams | None = None) -> Hierarchy:
             P, omega = Pt, 0.0
         R = from_scipy(P.csr().T, B, B)
         Ac = galerkin(R, A, P)
-        M = spai0(A) if prm.relax == "spai0" else jacobi(A, prm.jacobi_omega)
-        levels.append(Level(A=A, M=M, P=P, R=R, agg=agg))
+        S = None
+        if prm.relax == "ilut":
+            M = np.zeros((A.n_brows, B, B))
+            As = sp.csr_matrix(A.scipy())
+            As.eliminate_zeros()
+            S = ilut_mod.build(As, prm.ilut_p, prm.ilut_tau, prm.ilut_sweeps, prm.ilut_omega)
+        elif prm.relax == "spai0":
+            M = spai0(A)
+        else:
+            M = jacobi(A, prm.jacobi_omega)
+        levels.append(Level(A=A, M=M, P=P, R=R, agg=agg, S=S))
         omegas.append(omega)
         A = Ac
         l += 1
@@ -251,6 +269,13 @@ def apply_M(M: np.ndarray, v: np.ndarray, transpose: bool = False) -> np.ndarray
     if transpose:
         return np.einsum("iba,ib->ia", M, vb).reshape(-1)
     return np.einsum("iab,ib->ia", M, vb).reshape(-1)
+
+
+def smooth(lev: Level, v: np.ndarray, transpose: bool = False) -> np.ndarray:
+    """The level's relaxation operator applied to v: M v, or S v for ILUT."""
+    if lev.S is not None:
+        return lev.S.apply(v, transpose)
+    return apply_M(lev.M, v, transpose)
 
 
 def vcycle(H: Hierarchy, f: np.ndarray, l: int = 0, transpose: bool = False) -> np.ndarray:
@@ -268,15 +293,15 @@ def vcycle(H: Hierarchy, f: np.ndarray, l: int = 0, transpose: bool = False) -> 
     x = np.zeros_like(f)
     for it in range(npre):
         if it == 0:
-            x = apply_M(lev.M, f, transpose)
+            x = smooth(lev, f, transpose)
         else:
-            x = x + apply_M(lev.M, f - A @ x, transpose)
+            x = x + smooth(lev, f - A @ x, transpose)
     r = f - A @ x
     fc = spmv(lev.R, r)
     ec = vcycle(H, fc, l + 1, transpose)
     x = x + spmv(lev.P, ec)
     for it in range(npost):
-        x = x + apply_M(lev.M, f - A @ x, transpose)
+        x = x + smooth(lev, f - A @ x, transpose)
     return x
 
 
