@@ -9,9 +9,13 @@ triangular solves are carried out; the readings used here are:
    level's nonzeros, rows and columns in their natural order:
      w = a_i;  tau_i = tau * ||a_i||_2 (sum of squares in column order);
      for k < i with w_k != 0, in increasing k (fill included):
-         w_k = w_k / u_kk;  if |w_k| < tau_i: w_k = 0 and skip;
+         if |w_k| < tau_i: w_k = 0 and skip;  else w_k = w_k / u_kk;
          w_j -= w_k * u_kj for the strictly upper entries j of U's row k;
-     drop every off-diagonal w_j with |w_j| < tau_i;
+     drop every upper w_j (j > i) with |w_j| < tau_i;
+   A lower entry is tested before its division by the pivot, in the units
+   of a_i as the upper entries are: Saad tests the multiplier itself,
+   which on a matrix whose entries are far from 1 (the FD levels scale as
+   1/h^2) drops every multiplier and leaves no L at all.
      keep the floor(p * nnz_L(a_i)) largest |w_j|, j < i, and the
      floor(p * nnz_U(a_i)) largest, j > i (p a fill factor relative to
      the row's own lower / upper counts, so a row with no upper entries
@@ -106,14 +110,14 @@ def ilut(A: sp.spmatrix, p: float = 2.0, tau: float = 1e-2) -> tuple:
                 break
             k = min(pend)
             done.add(k)
-            wk = w[k] / d[k]
-            if abs(wk) < tau_i:
+            if abs(w[k]) < tau_i:
                 w[k] = 0.0
                 continue
+            wk = w[k] / d[k]
             w[k] = wk
             for j, ukj in Urows[k]:
                 w[j] = w.get(j, 0.0) - wk * ukj
-        lower = [(j, v) for j, v in w.items() if j < i and v != 0.0 and abs(v) >= tau_i]
+        lower = [(j, v) for j, v in w.items() if j < i and v != 0.0]
         upper = [(j, v) for j, v in w.items() if j > i and v != 0.0 and abs(v) >= tau_i]
         Lrows.append(_keep_largest(lower, int(math.floor(p * nzL))))
         Urows.append(_keep_largest(upper, int(math.floor(p * nzU))))

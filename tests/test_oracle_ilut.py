@@ -60,10 +60,10 @@ def test_tridiagonal_is_the_thomas_recurrence():
 
 
 def test_drop_rule_hand_example():
-    """Row 2's multiplier 0.02/4 = 0.005 is below tau ||a_2|| = 0.01 *
-    sqrt(0.0004 + 1 + 16) = 0.0412 and is dropped with its update; the
-    multiplier 1/3.75 survives.  By hand: u_11 = 4 - 0.25 = 3.75,
-    u_22 = 4 - 1/3.75."""
+    """Row 2's entry 0.02 (tested before the division by its pivot) is
+    below tau ||a_2|| = 0.01 * sqrt(0.0004 + 1 + 16) = 0.0412 and is
+    dropped with its update; the entry 1 survives, multiplier 1/3.75.  By
+    hand: u_11 = 4 - 0.25 = 3.75, u_22 = 4 - 1/3.75."""
     A = sp.csr_matrix(np.array([[4.0, 1.0, 0.0], [1.0, 4.0, 1.0], [0.02, 1.0, 4.0]]))
     L, d, U = ilut.ilut(A, p=2.0, tau=0.01)
     np.testing.assert_allclose(d, [4.0, 3.75, 4.0 - 1.0 / 3.75], rtol=1e-15)
@@ -90,6 +90,23 @@ def test_fill_factor_keeps_the_largest_entries():
     L1, d1, U1 = ilut.ilut(A, p=1.0, tau=0.0)
     np.testing.assert_array_equal(L1.toarray()[3, :3], [0.25, 0.0, 0.0])
     assert d1[3] == 8.0
+
+
+def test_lower_drop_test_is_scale_free():
+    """Scaling A by 2^-14 (exact in binary) scales U and D by 2^-14 and
+    leaves L unchanged bit for bit: the lower entries are tested before
+    the division by the pivot, so every decision compares quantities of
+    the same scale."""
+    s = si.make_system("c3", N=5)
+    A = schur.split(bsr.from_arrays(s.indptr, s.indices, s.data, 4), 3).A.csr()
+    A = sp.csr_matrix(A)
+    A.eliminate_zeros()
+    L1, d1, U1 = ilut.ilut(A)
+    sc = 2.0 ** -14
+    L2, d2, U2 = ilut.ilut(A * sc)
+    assert L1.nnz > 0 and L1.nnz == L2.nnz and (L1 != L2).nnz == 0
+    np.testing.assert_array_equal(d2, d1 * sc)
+    np.testing.assert_array_equal(U2.toarray(), U1.toarray() * sc)
 
 
 def test_sweeps_are_exact_once_they_outnumber_the_rows():
