@@ -56,7 +56,7 @@ typedef enum {
 enum { GBS_PC_AMG = 0, GBS_PC_SCHUR = 1 };
 enum { GBS_BICGSTAB = 0, GBS_GMRES = 1, GBS_IDRS = 2 };
 enum { GBS_FP64 = 0, GBS_FP32 = 1, GBS_BF16 = 2 };
-enum { GBS_SPAI0 = 0, GBS_JACOBI = 1 };
+enum { GBS_SPAI0 = 0, GBS_JACOBI = 1, GBS_ILUT = 2 };
 
 /* A square or rectangular block-CSR matrix in HOST memory.
  * row_ptr: int32[n_brows + 1], monotone, row_ptr[0] = 0.
@@ -116,6 +116,16 @@ typedef struct {
                              solvers; 1..8).  The shadow space is SplitMix64
                              (seed idr_seed) orthonormalised by MGS */
   int32_t idr_seed;
+  /* ILUT relaxation (relax or relax_p = GBS_ILUT; the velocity smoother of
+   * Section 4, Listings V2-V4): Saad's dual-threshold incomplete LU of each
+   * level's scalar nonzeros, keeping per row at most ilut_p times the
+   * row's own lower and upper counts of entries above ilut_tau times the
+   * row's 2-norm; each triangular solve is ilut_sweeps Jacobi sweeps; the
+   * step is x += ilut_omega (LU)^-1 (f - A x). */
+  double ilut_p;          /* fill factor (2) */
+  double ilut_tau;        /* drop tolerance (1e-2) */
+  int32_t ilut_sweeps;    /* Jacobi sweeps per triangular solve (2; 0..16) */
+  double ilut_omega;      /* damping (1) */
 } gbs_params;
 
 typedef struct {
@@ -214,7 +224,10 @@ gbs_status gbs_outer_format(const gbs_hierarchy* h, int32_t* format, int64_t* st
 /* Copy level l (0 = finest) of AMG `which` to host arrays.  part: 0 = A,
  * 1 = P, 2 = R, 3 = smoother blocks M (row_ptr/col_idx untouched),
  * 4 = aggregate ids (written to col_idx, n_brows entries), 5 = dense
- * coarse inverse (vals, n*n, row-major; level must be the coarsest).
+ * coarse inverse (vals, n*n, row-major; level must be the coarsest);
+ * for a level relaxed by ILUT, scalar CSR over the level's scalar
+ * unknowns: 6 = L (strictly lower; the factor's diagonal is 1), 7 = U
+ * (strictly upper), 8 = the diagonal of U (vals, n_brows entries).
  * Pass NULL arrays to query sizes: *n_brows, *n_bcols, *nnzb are always
  * written.  Values are the FP64 setup values (before any cast). */
 gbs_status gbs_export_level(const gbs_hierarchy* h, int32_t which, int32_t level,
@@ -226,8 +239,9 @@ gbs_status gbs_export_level(const gbs_hierarchy* h, int32_t which, int32_t level
  * running the setup: A[0..nlev-1] (A[0] = K), P[0..nlev-2], R[0..nlev-2],
  * M[0..nlev-2] smoother blocks (double[n_brows_l * bdim^2] each), and
  * the dense coarse inverse Ainv (double[n_L^2], row-major, n_L the
- * scalar size of A[nlev-1]).  Other arguments as gbs_build_hierarchy
- * (params->precond must be GBS_PC_AMG). */
+ * scalar size of A[nlev-1]).  With params->relax = GBS_ILUT, M may be
+ * NULL: the ILUT factors are computed here from each A[l].  Other
+ * arguments as gbs_build_hierarchy (params->precond must be GBS_PC_AMG). */
 gbs_status gbs_import_hierarchy(const gbs_bsr* A, const gbs_bsr* P, const gbs_bsr* R,
                                 const double* const* M, const double* Ainv, int32_t nlev,
                                 const gbs_params* params, void* stream,

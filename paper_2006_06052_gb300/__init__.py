@@ -29,7 +29,7 @@ GBS_OK, GBS_NOT_CONVERGED = 0, 1
 GBS_PC_AMG, GBS_PC_SCHUR = 0, 1
 GBS_BICGSTAB, GBS_GMRES, GBS_IDRS = 0, 1, 2
 GBS_FP64, GBS_FP32, GBS_BF16 = 0, 1, 2
-GBS_SPAI0, GBS_JACOBI = 0, 1
+GBS_SPAI0, GBS_JACOBI, GBS_ILUT = 0, 1, 2
 
 STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "INVALID", -2: "CUDA", -3: "OOM",
           -4: "BREAKDOWN", -5: "NAN"}
@@ -63,6 +63,8 @@ class Params(ctypes.Structure):
         ("setup_only", ctypes.c_int32), ("level_format", ctypes.c_int32),
         ("schur_p", ctypes.c_int32), ("schur_order", ctypes.c_int32),
         ("idr_s", ctypes.c_int32), ("idr_seed", ctypes.c_int32),
+        ("ilut_p", ctypes.c_double), ("ilut_tau", ctypes.c_double),
+        ("ilut_sweeps", ctypes.c_int32), ("ilut_omega", ctypes.c_double),
     ]
 
 
@@ -383,7 +385,8 @@ def export_level_sizes(H: Hierarchy, which: int, level: int, part: int):
 
 def export_level(H: Hierarchy, which: int, level: int, part: int):
     """Host copy of one level piece: part 0 A, 1 P, 2 R -> (indptr, indices, vals
-    [nnzb, B, B], n_bcols); 3 -> M [n, B, B]; 4 -> aggregate ids; 5 -> dense Ainv."""
+    [nnzb, B, B], n_bcols); 3 -> M [n, B, B]; 4 -> aggregate ids; 5 -> dense Ainv;
+    ILUT levels: 6 L, 7 U (scalar CSR: indptr, indices, vals, n) and 8 the diagonal."""
     lib = load_library()
     nbr, nbc, nnzb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
     args = (H.handle, which, level, part, ctypes.byref(nbr), ctypes.byref(nbc), ctypes.byref(nnzb))
@@ -392,6 +395,16 @@ def export_level(H: Hierarchy, which: int, level: int, part: int):
         B = H.params.nvel if which == 0 else 1
     else:
         B = H.bdim
+    if part in (6, 7):
+        ptr = np.zeros(nbr.value + 1, dtype=np.int32)
+        col = np.zeros(nnzb.value, dtype=np.int32)
+        val = np.zeros(nnzb.value)
+        _check(lib.gbs_export_level(*args, ptr.ctypes.data, col.ctypes.data, val.ctypes.data))
+        return ptr, col, val, nbc.value
+    if part == 8:
+        val = np.zeros(nbr.value)
+        _check(lib.gbs_export_level(*args, None, None, val.ctypes.data))
+        return val
     if part in (0, 1, 2):
         ptr = np.zeros(nbr.value + 1, dtype=np.int32)
         col = np.zeros(nnzb.value, dtype=np.int32)

@@ -332,6 +332,13 @@ struct DevAmg {
     DevBsr<VT> A, Pm, R;
     DevCsr<VT> Ac, Pc, Rc;              // scalar CSR forms (per-level format choice)
     DevSell<VT> As, Ps, Rs;             // sliced forms of the scalar CSR operators
+    // ILUT relaxation: L strictly lower, Us = D^-1 U strictly upper, their
+    // transposes (adjoint), D^-1, and three work vectors
+    bool ilu = false;
+    DevCsr<VT> Li, Ui, LiT, UiT;
+    const VT* dinv = nullptr;
+    ST *wa = nullptr, *wb = nullptr, *wc = nullptr;
+    int64_t nnz_Li = 0, nnz_Ui = 0;
     bool a_csr = false, p_csr = false, r_csr = false;
     bool a_sell = false, p_sell = false, r_sell = false;
     const VT* M = nullptr;
@@ -344,6 +351,8 @@ struct DevAmg {
   };
   int B = 1;
   int npre = 1, npost = 1;
+  int ilu_sweeps = 2;
+  double ilu_omega = 1.0;
   std::vector<Lev> lev;        // lev.back() is the coarsest (no A/P/R/M used)
   const ST* Ainv = nullptr;    // coarse inverse (ST precision)
   const ST* AinvT = nullptr;
@@ -354,6 +363,8 @@ struct DevAmg {
     B = H.B;
     npre = o.npre;
     npost = o.npost;
+    ilu_sweeps = o.ilut_sweeps;
+    ilu_omega = o.ilut_omega;
     std::vector<std::vector<VT>> keep;
     for (size_t l = 0; l < H.levels.size(); ++l) {
       const HLevel& h = H.levels[l];
@@ -388,6 +399,28 @@ struct DevAmg {
       else L.R = upload_bsr<VT, AT>(ar, h.R, false, s, keep);
       keep.push_back(cast_vec<VT>(h.M));
       L.M = ar.upload(keep.back().data(), keep.back().size(), s);
+      if (!h.ilu.d.empty()) {
+        L.ilu = true;
+        HCsr Us = h.ilu.U;
+        for (int i = 0; i < Us.n; ++i)
+          for (int k = Us.ptr[i]; k < Us.ptr[i + 1]; ++k) Us.val[k] /= h.ilu.d[i];
+        std::vector<double> di(h.ilu.d.size());
+        for (size_t i = 0; i < di.size(); ++i) di[i] = 1.0 / h.ilu.d[i];
+        L.Li = upload_csr<VT>(ar, h.ilu.L, s, keep);
+        L.Ui = upload_csr<VT>(ar, Us, s, keep);
+        if (o.tmaps) {
+          L.LiT = upload_csr<VT>(ar, transpose(h.ilu.L), s, keep);
+          L.UiT = upload_csr<VT>(ar, transpose(Us), s, keep);
+        }
+        keep.push_back(cast_vec<VT>(di));
+        L.dinv = ar.upload(keep.back().data(), keep.back().size(), s);
+        L.wa = ar.alloc<ST>(L.n);
+        L.wb = ar.alloc<ST>(L.n);
+        L.wc = ar.alloc<ST>(L.n);
+        L.nnz_Li = (int64_t)h.ilu.L.col.size();
+        L.nnz_Ui = (int64_t)h.ilu.U.col.size();
+        GBS_CUDA(cudaStreamSynchronize(s));  // host staging (Us, transposes) dies here
+      }
       L.f = ar.alloc<ST>(L.n);
       L.r = ar.alloc<ST>(L.n);
       L.x = ar.alloc<ST>(L.n);
@@ -419,6 +452,33 @@ struct DevAmg {
 
   int64_t n0() const { return lev[0].n; }
 
+  // z = S r with S the approximate (LU)^-1 of an ILUT level (S^T when TR):
+  // ilu_sweeps Jacobi sweeps per triangular solve.  Returns the buffer
+  // holding z (one of the level's work vectors; r may be any other vector).
+  template <bool TR>
+  const ST* ilu_apply(Lev& L, const ST* r, cudaStream_t s) {
+    const unsigned g = grid_for(L.n);
+    ST* pp[2] = {L.wa, L.wb};
+    int q = 0;
+    const ST* y = r;
+    const DevCsr<VT>& first = TR ? L.UiT : L.Li;
+    const DevCsr<VT>& second = TR ? L.LiT : L.Ui;
+    for (int k = 0; k < ilu_sweeps; ++k) {   // forward: y = r - L y; transposed: v = r - Us^T v
+      csr_spmv<SPMV_RESID, VT, ST, ST, AT>(first, y, r, pp[q], s);
+      y = pp[q];
+      q ^= 1;
+    }
+    k_vscale<VT, ST><<<g, 256, 0, s>>>(L.n, L.dinv, y, L.wc);   // D^-1 y
+    GBS_LAUNCH_CHECK();
+    const ST* z = L.wc;
+    for (int k = 0; k < ilu_sweeps; ++k) {   // forward: z = D^-1 y - Us z; transposed: t = t0 - L^T t
+      csr_spmv<SPMV_RESID, VT, ST, ST, AT>(second, z, L.wc, pp[q], s);
+      z = pp[q];
+      q ^= 1;
+    }
+    return z;
+  }
+
   // out = V(f) at level l; f and out are ST vectors of that level's size.
   template <bool TR>
   void cycle(size_t l, const ST* f, ST* out, cudaStream_t s) {
@@ -435,13 +495,31 @@ struct DevAmg {
     ST* x = L.x;
     ST* xt = L.xt;
     const bool acsr = L.a_csr && !TR;   // A^T goes through the block form's transpose map
+    const unsigned gv = grid_for(L.n);
     auto sweep = [&](const ST* xin, ST* xout) {
-      if (acsr && L.a_sell) sell_relax<VT, ST, AT>(B, L.As, L.M, f, xin, xout, s);
-      else if (acsr) csr_relax<VT, ST, AT>(B, L.Ac, L.M, f, xin, xout, s);
-      else relax<TR, VT, ST, AT>(B, L.A, L.M, f, xin, xout, s);
+      if (L.ilu) {   // xout = xin + omega S (f - A xin)
+        if (acsr && L.a_sell) sell_spmv<SPMV_RESID, VT, ST, ST, AT>(L.As, xin, f, L.r, s);
+        else if (acsr) csr_spmv<SPMV_RESID, VT, ST, ST, AT>(L.Ac, xin, f, L.r, s);
+        else spmv<TR, SPMV_RESID, VT, ST, ST, AT>(B, L.A, xin, f, L.r, s);
+        const ST* z = ilu_apply<TR>(L, L.r, s);
+        k_vaxpy<ST><<<gv, 256, 0, s>>>(L.n, xin, (ST)ilu_omega, z, xout);
+        GBS_LAUNCH_CHECK();
+      } else if (acsr && L.a_sell) {
+        sell_relax<VT, ST, AT>(B, L.As, L.M, f, xin, xout, s);
+      } else if (acsr) {
+        csr_relax<VT, ST, AT>(B, L.Ac, L.M, f, xin, xout, s);
+      } else {
+        relax<TR, VT, ST, AT>(B, L.A, L.M, f, xin, xout, s);
+      }
     };
     if (pre >= 1) {
-      mapply<TR, VT, ST, AT>(B, nb, L.M, f, x, s);
+      if (L.ilu) {
+        const ST* z = ilu_apply<TR>(L, f, s);
+        k_vaxpy<ST><<<gv, 256, 0, s>>>(L.n, (const ST*)nullptr, (ST)ilu_omega, z, x);
+        GBS_LAUNCH_CHECK();
+      } else {
+        mapply<TR, VT, ST, AT>(B, nb, L.M, f, x, s);
+      }
       for (int it = 1; it < pre; ++it) {
         sweep(x, xt);
         std::swap(x, xt);
@@ -490,13 +568,20 @@ struct DevAmg {
                             : L.r_csr ? L.nnz_R * (sv + 4) + 4 * (nc * B + 1)
                                       : L.nnzb_R * (B * B * sv + 4) + 4 * (nc + 1);
       const double Mbytes = nb * B * B * sv;
-      // mapply (M, f, x) + resid (A, x, f, r) + restrict (R, r, fc)
-      // + prolong (P, ec, x rw) + relax (A, M, f, x, out)
-      b += Mbytes + 2 * L.n * sx;
-      b += Abytes + 3 * L.n * sx;
-      b += Rbytes + L.n * sx + lev[l + 1].n * sx;
-      b += Pbytes + lev[l + 1].n * sx + 2 * L.n * sx;
-      b += Abytes + Mbytes + 3 * L.n * sx;
+      b += Abytes + 3 * L.n * sx;                               // resid (A, x, f, r)
+      b += Rbytes + L.n * sx + lev[l + 1].n * sx;               // restrict (R, r, fc)
+      b += Pbytes + lev[l + 1].n * sx + 2 * L.n * sx;           // prolong (P, ec, x rw)
+      if (L.ilu) {
+        const double m = ilu_sweeps;
+        const double ilu = m * (L.nnz_Li * (sv + 4) + 4 * (L.n + 1.0) + 3 * L.n * sx) +
+                           (L.n * sv + 2 * L.n * sx) +
+                           m * (L.nnz_Ui * (sv + 4) + 4 * (L.n + 1.0) + 3 * L.n * sx);
+        b += ilu + 2 * L.n * sx;                                 // zero-guess step
+        b += Abytes + 3 * L.n * sx + ilu + 3 * L.n * sx;          // resid + S + axpy
+      } else {
+        b += Mbytes + 2 * L.n * sx;                              // mapply (M, f, x)
+        b += Abytes + Mbytes + 3 * L.n * sx;                     // relax (A, M, f, x, out)
+      }
     }
     b += (double)nc * nc * sx + 2.0 * nc * sx;
     return b;

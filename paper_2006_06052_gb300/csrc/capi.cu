@@ -115,12 +115,19 @@ void check_params(const gbs_params* p) {
   if (p->replace_every < 1) throw SetupError{"replace_every must be >= 1"};
   if (p->precision < GBS_FP64 || p->precision > GBS_BF16) throw SetupError{"bad precision"};
   if (p->npre < 0 || p->npost < 1) throw SetupError{"need npre >= 0 and npost >= 1"};
-  if (p->relax != GBS_SPAI0 && p->relax != GBS_JACOBI) throw SetupError{"bad relax"};
-  if (p->relax_p != GBS_SPAI0 && p->relax_p != GBS_JACOBI) throw SetupError{"bad relax_p"};
+  if (p->relax != GBS_SPAI0 && p->relax != GBS_JACOBI && p->relax != GBS_ILUT)
+    throw SetupError{"bad relax"};
+  if (p->relax_p != GBS_SPAI0 && p->relax_p != GBS_JACOBI && p->relax_p != GBS_ILUT)
+    throw SetupError{"bad relax_p"};
+  if (p->precond == GBS_PC_SCHUR && p->schur_p == 1 && p->relax_p == GBS_ILUT)
+    throw SetupError{"the single-sweep pressure solve (schur_p = 1) takes SPAI0 or Jacobi"};
+  if (!(p->ilut_p >= 0.0) || !(p->ilut_tau >= 0.0) || !(p->ilut_omega > 0.0) ||
+      p->ilut_sweeps < 0 || p->ilut_sweeps > 16)
+    throw SetupError{"bad ILUT parameters (p >= 0, tau >= 0, omega > 0, sweeps 0..16)"};
   if (p->max_levels < 1 || p->coarse_enough < 1) throw SetupError{"bad level limits"};
   if (p->precond == GBS_PC_SCHUR && (p->nvel < 1 || p->nvel > 3))
     throw SetupError{"nvel must be in 1..3"};
-  if (p->level_format < 0 || p->level_format > 1) throw SetupError{"level_format must be 0 or 1"};
+  if (p->level_format < 0 || p->level_format > 3) throw SetupError{"level_format must be 0..3"};
   if (p->schur_p < 0 || p->schur_p > 1) throw SetupError{"schur_p must be 0 or 1"};
   if (p->schur_order < 0 || p->schur_order > 1) throw SetupError{"schur_order must be 0 or 1"};
 }
@@ -134,6 +141,8 @@ AmgSetupParams amg_prm(const gbs_params* p, int relax) {
   a.jacobi_omega = p->jacobi_omega;
   a.smooth_P = p->smooth_P != 0;
   a.power_iters = p->power_iters;
+  a.ilut_p = p->ilut_p;
+  a.ilut_tau = p->ilut_tau;
   return a;
 }
 
@@ -146,6 +155,8 @@ PrecondOptions pc_opts(const gbs_params* p) {
   o.level_format = p->level_format;
   o.schur_order = p->schur_order;
   o.schur_p_smoother = p->schur_p == 1;
+  o.ilut_sweeps = p->ilut_sweeps;
+  o.ilut_omega = p->ilut_omega;
   return o;
 }
 
@@ -891,6 +902,10 @@ gbs_status gbs_params_default(gbs_params* p) {
   p->schur_order = 0;
   p->idr_s = 5;
   p->idr_seed = 0;
+  p->ilut_p = 2.0;
+  p->ilut_tau = 1e-2;
+  p->ilut_sweeps = 2;
+  p->ilut_omega = 1.0;
   return GBS_OK;
 }
 
@@ -935,7 +950,8 @@ gbs_status gbs_import_hierarchy(const gbs_bsr* A, const gbs_bsr* P, const gbs_bs
     *out = nullptr;
     check_params(params);
     if (params->precond != GBS_PC_AMG) throw SetupError{"import supports the AMG preconditioner"};
-    if (nlev < 1 || !A || !Ainv || (nlev > 1 && (!P || !R || !M)))
+    if (nlev < 1 || !A || !Ainv ||
+        (nlev > 1 && (!P || !R || (!M && params->relax != GBS_ILUT))))
       throw SetupError{"bad level arrays"};
     init_device();
     auto hh = std::make_unique<gbs_hierarchy>();
@@ -960,8 +976,13 @@ gbs_status gbs_import_hierarchy(const gbs_bsr* A, const gbs_bsr* P, const gbs_bs
         throw SetupError{"all levels need the same bdim"};
       if (L.P.nbr != L.A.nbr || L.P.nbc != An.nbr || L.R.nbr != An.nbr || L.R.nbc != L.A.nbr)
         throw SetupError{"level " + std::to_string(l) + ": P/R shapes do not match A"};
-      if (!M[l]) throw SetupError{"null smoother blocks"};
-      L.M.assign(M[l], M[l] + (size_t)L.A.nbr * H.B * H.B);
+      if (params->relax == GBS_ILUT) {
+        // the factors are this library's own, from the imported operator
+        L.ilu = ilut(to_scalar_csr(L.A), params->ilut_p, params->ilut_tau);
+      } else {
+        if (!M[l]) throw SetupError{"null smoother blocks"};
+        L.M.assign(M[l], M[l] + (size_t)L.A.nbr * H.B * H.B);
+      }
       H.levels.push_back(std::move(L));
     }
     H.Ac = from_c(&A[nlev - 1]);
@@ -1150,6 +1171,25 @@ gbs_status gbs_export_level(const gbs_hierarchy* hh, int32_t which, int32_t leve
       *nnzb = 0;
       if (part == 3 && vals) std::memcpy(vals, L.M.data(), sizeof(double) * L.M.size());
       if (part == 4 && col_idx) std::memcpy(col_idx, L.agg.data(), sizeof(int32_t) * L.agg.size());
+      return GBS_OK;
+    }
+    if (part >= 6 && part <= 8) {
+      if (coarsest) throw SetupError{"the coarsest level has no smoother"};
+      const HIlu& F = H.levels[level].ilu;
+      if (F.d.empty()) throw SetupError{"the level is not relaxed by ILUT"};
+      const int n = (int)F.d.size();
+      *n_brows = n;
+      *n_bcols = part == 8 ? 1 : n;
+      if (part == 8) {
+        *nnzb = 0;
+        if (vals) std::memcpy(vals, F.d.data(), sizeof(double) * F.d.size());
+        return GBS_OK;
+      }
+      const HCsr& C = part == 6 ? F.L : F.U;
+      *nnzb = (int64_t)C.col.size();
+      if (row_ptr) std::memcpy(row_ptr, C.ptr.data(), sizeof(int32_t) * C.ptr.size());
+      if (col_idx) std::memcpy(col_idx, C.col.data(), sizeof(int32_t) * C.col.size());
+      if (vals) std::memcpy(vals, C.val.data(), sizeof(double) * C.val.size());
       return GBS_OK;
     }
     if (part == 5) {

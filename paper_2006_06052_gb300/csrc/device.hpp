@@ -85,6 +85,8 @@ struct PrecondOptions {
   int schur_order = 0;   // 0 full (two velocity solves), 1 lower (one)
   bool schur_p_smoother = false;  // pressure solve = one smoother application (HSchur::MS)
   double* err = nullptr;          // device slot a timed-out pipelined kernel sets to 1.0
+  int ilut_sweeps = 2;            // Jacobi sweeps per ILUT triangular solve
+  double ilut_omega = 1.0;        // ILUT relaxation damping
 };
 
 std::unique_ptr<DevPrecond> make_amg_precond(const HAmg& H, const PrecondOptions& o,

@@ -246,6 +246,12 @@ struct Geom {
 // long rows.
 // Row split S for one-lane-per-scalar-row levels: long rows are shared by
 // S lanes (one FP add per reduction step).
+// Small levels are latency-bound: a level with fewer than LANES_TARGET
+// lanes (a quarter of the threads the 152 SMs hold) splits its rows
+// further, as long as each lane keeps at least one block.  (Measured on
+// C2: the level-2 prolongator, 8k lanes at S = 1, drops from 14 to 6 us at
+// S = 8; the level-1 prolongator, 127k lanes, is slower at S = 2.)
+constexpr int64_t LANES_TARGET = 152 * 512;
 template <int B>
 inline int choose_split(int64_t nbr, int64_t nnzb) {
   const double avg = nbr ? (double)nnzb / nbr : 0.0;
@@ -253,6 +259,7 @@ inline int choose_split(int64_t nbr, int64_t nnzb) {
   if (avg >= 12.0) S = 2;
   if (avg >= 24.0) S = 4;
   if (avg >= 48.0) S = 8;
+  while (S < 8 && B * S * 2 <= 32 && 2.0 * S <= avg && nbr * B * S < LANES_TARGET) S *= 2;
   while (S > 1 && B * S > 32) S >>= 1;
   return S;
 }
@@ -265,7 +272,8 @@ inline int choose_group(int64_t nbr, int64_t nnzb) {
   if (sizeof(AT) == 8 || !Gm::FIXED) {
     // FP64 (pipe-bound) and 3x3 / scalar FP32-BF16 rows: one lane per
     // scalar row with a row split (choose_split); a CTA per row only for a
-    // few very long rows
+    // few very long rows (a CTA per row measured 3x slower than a warp per
+    // row on the 2017-row level 2 of C2)
     if (nbr <= 1024 && avg >= 128.0) return 256;
     return 0;
   }
@@ -669,6 +677,24 @@ __global__ void k_cast<float, double>(int64_t n, const float* __restrict__ in,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (double)in[i];
+}
+
+// out = s .* in (ILUT: scaling by D^-1).
+template <class VT, class ST>
+__global__ void k_vscale(int64_t n, const VT* __restrict__ sc, const ST* __restrict__ in,
+                         ST* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = cvt<ST>(sc[i]) * in[i];
+}
+
+// out = x + w z (x null: out = w z).
+template <class ST>
+__global__ void k_vaxpy(int64_t n, const ST* __restrict__ x, ST w, const ST* __restrict__ z,
+                        ST* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = x ? x[i] + w * z[i] : w * z[i];
 }
 
 inline unsigned grid_for(int64_t threads, int tpb = 256) {

@@ -349,36 +349,78 @@ static __global__ void __launch_bounds__(RED_THREADS, 4)
 }
 
 // ------------------------------------------------------------------ GMRES
-// h[i] = V_i . w for i < J (chunks of 8 vectors), and sc[S_WW0] = w . w.
-// gate: if non-null and *gate == 0 the kernel does nothing.
+// Partial dots of one pass over the CHN vectors V0 + q n (q < CHN) against
+// w, plus w . w when WW: no branch in the element loop, so each element's
+// loads issue together (a per-vector bounds test there serialised the
+// loads and ran the kernel at a third of the bandwidth).  Block sums go to
+// out[0..CHN) and, with WW, to ww_out.
+template <int CHN, bool WW>
+__device__ __forceinline__ void multidot_pass(int64_t n, const double* __restrict__ V0,
+                                              const double* __restrict__ w, double* out,
+                                              double* ww_out, double (*sh)[8]) {
+  double v[CHN + 1];
+#pragma unroll
+  for (int q = 0; q <= CHN; ++q) v[q] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+    double a[CHN > 0 ? CHN : 1];
+#pragma unroll
+    for (int q = 0; q < CHN; ++q) a[q] = V0[(size_t)q * n + i];
+#pragma unroll
+    for (int q = 0; q < CHN; ++q) v[q] += a[q] * wi;
+    if constexpr (WW) v[CHN] += wi * wi;
+  }
+  double t[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) t[q] = q <= CHN ? v[q <= CHN ? q : 0] : 0.0;
+  block_sum<8>(t, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < CHN; ++q) out[q] = t[q];
+    if constexpr (WW) *ww_out = t[CHN];
+  }
+  __syncthreads();
+}
+
+// h[i] = V_i . w for i < J, and sc[S_WW0] = w . w: passes of 7 (the first
+// also forms w . w), 8, 4, 2, 1 vectors, so no FP64 work goes to padding.
 static __global__ void __launch_bounds__(RED_THREADS, 4)
     k_multidot(int64_t n, const double* __restrict__ V, int J, const double* __restrict__ w,
                double* __restrict__ h, Red R, int slot, const double* __restrict__ gate) {
   if (gate && *gate == 0.0) return;
-  constexpr int CH = 8;
-  __shared__ double sh[RED_THREADS / 32][CH];
+  __shared__ double sh[RED_THREADS / 32][8];
   __shared__ bool last;
-  const int nch = (J + 1 + CH - 1) / CH;  // J dots + w.w
-  for (int c0 = 0; c0 < nch; ++c0) {
-    double v[CH];
-#pragma unroll
-    for (int q = 0; q < CH; ++q) v[q] = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      const double wi = w[i];
-#pragma unroll
-      for (int q = 0; q < CH; ++q) {
-        const int vi = c0 * CH + q;
-        if (vi < J) v[q] += V[(size_t)vi * n + i] * wi;
-        else if (vi == J) v[q] += wi * wi;
-      }
+  const int nv = J + 1;   // partial slot J holds w . w
+  double* part = R.partials + (size_t)blockIdx.x * MAX_DOTS;
+  // first pass: up to 7 vectors and w . w
+  int v0 = J < 7 ? J : 7;
+  switch (v0) {
+    case 0: multidot_pass<0, true>(n, V, w, part, part + J, sh); break;
+    case 1: multidot_pass<1, true>(n, V, w, part, part + J, sh); break;
+    case 2: multidot_pass<2, true>(n, V, w, part, part + J, sh); break;
+    case 3: multidot_pass<3, true>(n, V, w, part, part + J, sh); break;
+    case 4: multidot_pass<4, true>(n, V, w, part, part + J, sh); break;
+    case 5: multidot_pass<5, true>(n, V, w, part, part + J, sh); break;
+    case 6: multidot_pass<6, true>(n, V, w, part, part + J, sh); break;
+    default: multidot_pass<7, true>(n, V, w, part, part + J, sh); break;
+  }
+  while (v0 < J) {
+    const int left = J - v0;
+    const double* V0 = V + (size_t)v0 * n;
+    if (left >= 8) {
+      multidot_pass<8, false>(n, V0, w, part + v0, nullptr, sh);
+      v0 += 8;
+    } else if (left >= 4) {
+      multidot_pass<4, false>(n, V0, w, part + v0, nullptr, sh);
+      v0 += 4;
+    } else if (left >= 2) {
+      multidot_pass<2, false>(n, V0, w, part + v0, nullptr, sh);
+      v0 += 2;
+    } else {
+      multidot_pass<1, false>(n, V0, w, part + v0, nullptr, sh);
+      v0 += 1;
     }
-    block_sum<CH>(v, sh);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int q = 0; q < CH; ++q) R.partials[(size_t)blockIdx.x * MAX_DOTS + c0 * CH + q] = v[q];
-    }
-    __syncthreads();
   }
   if (threadIdx.x == 0) {
     __threadfence();
@@ -388,19 +430,20 @@ static __global__ void __launch_bounds__(RED_THREADS, 4)
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int c0 = 0; c0 < nch; ++c0) {
-    double s[CH];
+  for (int c0 = 0; c0 < nv; c0 += 8) {
+    double s[8];
 #pragma unroll
-    for (int q = 0; q < CH; ++q) s[q] = 0.0;
+    for (int q = 0; q < 8; ++q) s[q] = 0.0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
 #pragma unroll
-      for (int q = 0; q < CH; ++q) s[q] += __ldcg(R.partials + (size_t)b * MAX_DOTS + c0 * CH + q);
+      for (int q = 0; q < 8; ++q)
+        if (c0 + q < nv) s[q] += __ldcg(R.partials + (size_t)b * MAX_DOTS + c0 + q);
     }
-    block_sum<CH>(s, sh);
+    block_sum<8>(s, sh);
     if (threadIdx.x == 0) {
 #pragma unroll
-      for (int q = 0; q < CH; ++q) {
-        const int vi = c0 * CH + q;
+      for (int q = 0; q < 8; ++q) {
+        const int vi = c0 + q;
         if (vi < J) h[vi] = s[q];
         else if (vi == J) R.sc[S_WW0] = s[q];
       }

@@ -21,6 +21,7 @@
 #include "setup.hpp"
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 
@@ -438,7 +439,8 @@ HAmg build_amg(const HBsr& A0, const AmgSetupParams& prm) {
     HBsr R = transpose(P);
     HBsr AP = spgemm(A, P);
     HBsr Ac = spgemm(R, AP);
-    lev.M = prm.relax == 0 ? spai0(A) : jacobi(A, prm.jacobi_omega);
+    if (prm.relax == 2) lev.ilu = ilut(to_scalar_csr(A), prm.ilut_p, prm.ilut_tau);
+    else lev.M = prm.relax == 0 ? spai0(A) : jacobi(A, prm.jacobi_omega);
     lev.A = std::move(A);
     lev.P = std::move(P);
     lev.R = std::move(R);
@@ -584,6 +586,125 @@ HSell to_sell(const HCsr& C, int B) {
       }
     }
   return S;
+}
+
+HIlu ilut(const HCsr& A, double p, double tau) {
+  const int n = A.n;
+  if (A.ncols != n) fail("ILUT needs a square matrix");
+  HIlu F;
+  F.L.n = F.U.n = n;
+  F.L.ncols = F.U.ncols = n;
+  F.L.ptr.assign(n + 1, 0);
+  F.U.ptr.assign(n + 1, 0);
+  F.d.assign(n, 0.0);
+  std::vector<double> w(n, 0.0);
+  std::vector<char> present(n, 0);
+  std::vector<int> cols;
+  std::vector<std::pair<int, double>> lower, upper;
+  auto keep = [](std::vector<std::pair<int, double>>& e, int count) {
+    if ((int)e.size() > count) {
+      std::sort(e.begin(), e.end(), [](const std::pair<int, double>& a,
+                                       const std::pair<int, double>& b) {
+        const double fa = std::fabs(a.second), fb = std::fabs(b.second);
+        return fa > fb || (fa == fb && a.first < b.first);
+      });
+      e.resize(count < 0 ? 0 : count);
+    }
+    std::sort(e.begin(), e.end());
+  };
+  for (int i = 0; i < n; ++i) {
+    cols.clear();
+    int nzL = 0, nzU = 0;
+    double s2 = 0.0;
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      const double v = A.val[k];
+      if (v == 0.0) continue;
+      const int j = A.col[k];
+      w[j] = v;
+      present[j] = 1;
+      cols.push_back(j);
+      s2 += v * v;
+      if (j < i) ++nzL;
+      else if (j > i) ++nzU;
+    }
+    const double tau_i = tau * std::sqrt(s2);
+    // lower columns in increasing order, fill included (a min-heap)
+    std::vector<int> heap;
+    for (int j : cols)
+      if (j < i) heap.push_back(j);
+    std::make_heap(heap.begin(), heap.end(), std::greater<int>());
+    while (!heap.empty()) {
+      std::pop_heap(heap.begin(), heap.end(), std::greater<int>());
+      const int k = heap.back();
+      heap.pop_back();
+      if (std::fabs(w[k]) < tau_i) {   // tested before the division (scale-free)
+        w[k] = 0.0;
+        continue;
+      }
+      const double wk = w[k] / F.d[k];
+      w[k] = wk;
+      for (int e = F.U.ptr[k]; e < F.U.ptr[k + 1]; ++e) {
+        const int j = F.U.col[e];
+        if (!present[j]) {
+          present[j] = 1;
+          w[j] = 0.0;
+          cols.push_back(j);
+          if (j < i) {
+            heap.push_back(j);
+            std::push_heap(heap.begin(), heap.end(), std::greater<int>());
+          }
+        }
+        w[j] -= wk * F.U.val[e];
+      }
+    }
+    lower.clear();
+    upper.clear();
+    for (int j : cols) {
+      const double v = w[j];
+      if (j == i || v == 0.0) continue;
+      if (j < i) lower.emplace_back(j, v);   // multipliers, tested during elimination
+      else if (std::fabs(v) >= tau_i) upper.emplace_back(j, v);
+    }
+    keep(lower, (int)std::floor(p * nzL));
+    keep(upper, (int)std::floor(p * nzU));
+    for (const auto& e : lower) {
+      F.L.col.push_back(e.first);
+      F.L.val.push_back(e.second);
+    }
+    for (const auto& e : upper) {
+      F.U.col.push_back(e.first);
+      F.U.val.push_back(e.second);
+    }
+    F.L.ptr[i + 1] = (int32_t)F.L.col.size();
+    F.U.ptr[i + 1] = (int32_t)F.U.col.size();
+    double di = present[i] ? w[i] : 0.0;
+    if (di == 0.0) di = tau_i != 0.0 ? tau_i : 1.0;
+    F.d[i] = di;
+    for (int j : cols) {
+      w[j] = 0.0;
+      present[j] = 0;
+    }
+  }
+  return F;
+}
+
+HCsr transpose(const HCsr& A) {
+  HCsr T;
+  T.n = A.ncols;
+  T.ncols = A.n;
+  T.ptr.assign(T.n + 1, 0);
+  for (int32_t c : A.col) ++T.ptr[c + 1];
+  for (int i = 0; i < T.n; ++i) T.ptr[i + 1] += T.ptr[i];
+  T.col.resize(A.col.size());
+  T.val.resize(A.val.size());
+  std::vector<int32_t> next(T.ptr.begin(), T.ptr.end() - 1);
+  for (int i = 0; i < A.n; ++i)
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      const int32_t at = next[A.col[k]]++;
+      T.col[at] = i;
+      T.val[at] = A.val[k];
+    }
+  return T;
 }
 
 double block_fill(const HBsr& A) {

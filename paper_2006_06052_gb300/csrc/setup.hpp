@@ -26,15 +26,32 @@ struct AmgSetupParams {
   double eps_strong = 0.08;
   int coarse_enough = 1000;
   int max_levels = 10;
-  int relax = 0;           // 0 SPAI0, 1 damped Jacobi
+  int relax = 0;           // 0 SPAI0, 1 damped Jacobi, 2 ILUT
   double jacobi_omega = 0.72;
   bool smooth_P = true;
   int power_iters = 20;
+  double ilut_p = 2.0;     // ILUT fill factor
+  double ilut_tau = 1e-2;  // ILUT drop tolerance
+};
+
+// Scalar CSR (declared here for the ILUT factors; see to_scalar_csr).
+struct HCsr {
+  int n = 0, ncols = 0;
+  std::vector<int32_t> ptr, col;
+  std::vector<double> val;
+};
+
+// ILUT factors of a scalar matrix: A ~ (I + L)(D + U), L strictly lower,
+// U strictly upper, D = diag(d).
+struct HIlu {
+  HCsr L, U;
+  std::vector<double> d;
 };
 
 struct HLevel {
   HBsr A, P, R;
-  std::vector<double> M;   // n_brows * B * B smoother blocks
+  std::vector<double> M;   // n_brows * B * B smoother blocks (SPAI0 / Jacobi)
+  HIlu ilu;                // ILUT relaxation factors (relax = 2)
   std::vector<int32_t> agg;
   double omega = 0.0;
 };
@@ -63,12 +80,20 @@ std::vector<double> jacobi(const HBsr& A, double omega);
 
 // Scalar CSR of the nonzero entries of a block matrix (columns sorted per
 // row); fill = nonzeros / stored block values.
-struct HCsr {
-  int n = 0, ncols = 0;
-  std::vector<int32_t> ptr, col;
-  std::vector<double> val;
-};
 HCsr to_scalar_csr(const HBsr& A);
+
+// Saad's dual-threshold ILUT (Section 4's velocity smoother), row by row
+// in natural order: eliminate the row's lower entries in increasing
+// column order (fill included), dropping an entry below tau * ||a_i||_2
+// (tested before its division by the pivot, so that the test is
+// scale-free) with its update; drop upper entries below the same bound;
+// keep the floor(p * count) largest of the lower and of the upper
+// entries, count being the row's own lower / upper nonzeros (ties to the
+// smaller column); a zero pivot becomes tau * ||a_i||_2 (1 if that is
+// zero).
+HIlu ilut(const HCsr& A, double p, double tau);
+// Transpose of a scalar CSR matrix (columns sorted per row).
+HCsr transpose(const HCsr& A);
 double block_fill(const HBsr& A);
 
 // Sliced scalar CSR: the rows of component c (c < B) of 32 consecutive

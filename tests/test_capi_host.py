@@ -171,3 +171,46 @@ def test_host_setup_plain_aggregation_matches_oracle():
     ptr, col, val, nbc = gb.export_level(Hc, 0, 0, 1)
     assert np.all(np.diff(ptr) == 1)                       # one block per row
     np.testing.assert_array_equal(val, np.broadcast_to(np.eye(3), val.shape))
+
+
+@pytest.mark.parametrize("case", ["c3_velocity", "c2_monolithic"])
+def test_host_ilut_factors_match_oracle(case):
+    """The C++ ILUT of every level (relax = ILUT) equals the oracle's ILUT
+    of the same exported level matrix: same drop and fill decisions (FP64,
+    same operation order), values to the last bit."""
+    from oracle import ilut
+    if case == "c3_velocity":
+        s = si.make_system("c3", N=7)
+        H = _host(s, precond=gb.GBS_PC_SCHUR, krylov=gb.GBS_GMRES, coarse_enough=40,
+                  relax=gb.GBS_ILUT)
+        which = 0
+    else:
+        s = si.make_system("c2", N=7)
+        H = _host(s, coarse_enough=40, relax=gb.GBS_ILUT)
+        which = 0
+    info = gb.hierarchy_info(H, which)
+    assert info["nlevels"] >= 2
+    for l in range(info["nlevels"] - 1):
+        ptr, col, val, nbc = gb.export_level(H, which, l, 0)
+        B = val.shape[1]
+        A = sp.bsr_matrix((val, col, ptr), shape=(len(ptr) - 1) * B * np.array([1, 1])).tocsr()
+        A.eliminate_zeros()
+        A.sort_indices()
+        Lo, do, Uo = ilut.ilut(A, p=2.0, tau=1e-2)
+        for part, Mo in ((6, Lo), (7, Uo)):
+            cp, cc, cv, n = gb.export_level(H, which, l, part)
+            assert n == A.shape[0]
+            np.testing.assert_array_equal(cp, Mo.indptr)
+            np.testing.assert_array_equal(cc, Mo.indices)
+            np.testing.assert_array_equal(cv, Mo.data)
+        np.testing.assert_array_equal(gb.export_level(H, which, l, 8), do)
+
+
+def test_ilut_parameters_validated():
+    s = si.make_system("c2", N=3)
+    with pytest.raises(gb.GbsError):
+        _host(s, relax=gb.GBS_ILUT, ilut_sweeps=17)
+    with pytest.raises(gb.GbsError):
+        _host(s, relax=gb.GBS_ILUT, ilut_omega=0.0)
+    with pytest.raises(gb.GbsError):
+        _host(s, precond=gb.GBS_PC_SCHUR, schur_p=1, relax_p=gb.GBS_ILUT)
