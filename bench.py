@@ -66,7 +66,7 @@ def solver_params(gb, wl, **kw):
     if name == "c3":
         kw.setdefault("krylov", gb.GBS_GMRES)
         return gb.params_default(precond=gb.GBS_PC_SCHUR, precision=prec, enable_adjoint=0, **kw)
-    relax = gb.GBS_SPAI0 if name == "c1" else gb.GBS_JACOBI
+    relax = kw.pop("relax", gb.GBS_SPAI0 if name == "c1" else gb.GBS_JACOBI)
     return gb.params_default(relax=relax, precision=prec, enable_adjoint=0, **kw)
 
 
@@ -313,6 +313,11 @@ def main():
                     help="outer solver (default: the workload's: BiCGStab for c1/c2, GMRES(30) for c3)")
     ap.add_argument("--level-format", type=int, default=0,
                     help="0 scalar CSR for mostly-zero block levels, 1 block form everywhere")
+    ap.add_argument("--plain-aggregation", action="store_true",
+                    help="unsmoothed aggregation (P = P_tent), the paper's velocity AMG")
+    ap.add_argument("--relax", default=None, choices=["spai0", "jacobi", "ilut"],
+                    help="smoother of the monolithic / velocity AMG (default: the workload's; "
+                         "ilut = the velocity smoother of the paper's Listings V2-V4)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -339,6 +344,11 @@ def main():
                            "idrs": gb.GBS_IDRS}[args.krylov]
     if spec["system"] == "c3":
         extra.update(schur_order=args.schur_order, schur_p=args.schur_p)
+    if args.relax:
+        extra["relax"] = {"spai0": gb.GBS_SPAI0, "jacobi": gb.GBS_JACOBI,
+                          "ilut": gb.GBS_ILUT}[args.relax]
+    if args.plain_aggregation:
+        extra["smooth_P"] = 0
     prm = solver_params(gb, wl, use_graph=0 if args.no_graph else 1, **extra)
     t0 = time.perf_counter()
     H = gb.build_hierarchy(s.indptr, s.indices, s.data, s.bdim, prm)
@@ -478,7 +488,8 @@ def main():
         "config": {"workload": spec["desc"], "l2": "inputs larger than L2 (K = %.0f MB)"
                    % (nnzb * (B * B * 8 + 4) / 1e6), "parallelism": "replicas" if world > 1 else "1gpu",
                    "iterations": iters[-1], "rel_res": rel_res, "converged": converged,
-                   "setup_s": setup_s, "graph": not args.no_graph, **extra},
+                   "setup_s": setup_s, "graph": not args.no_graph,
+                   **{k: (args.relax if k == "relax" else v) for k, v in extra.items()}},
         "e2e": {"value": e2e_ms / world, "unit": UNIT, "h2d_bytes_per_step": int(b.numel() * 8),
                 "d2h_bytes_per_step": int(x.numel() * 8)},
         "gpu_launches": int(launches),

@@ -36,25 +36,30 @@ namespace gbs {
 // above that would otherwise run a second, partial wave.
 inline unsigned resident_grid(const void* fn, int cap, int threads, size_t smem) {
   static std::mutex mu;
-  static std::map<std::pair<const void*, int>, unsigned> cache;
+  static std::map<std::pair<const void*, int>, int64_t> cache;   // CTAs resident per device
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return (unsigned)cap;
-  std::lock_guard<std::mutex> lock(mu);
-  const auto key = std::make_pair(fn, dev);
-  const auto it = cache.find(key);
-  if (it != cache.end()) return it->second;
-  int per_sm = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      per_sm < 1 || sms < 1) {
-    (void)cudaGetLastError();
-    return (unsigned)cap;
+  if (cudaGetDevice(&dev) != cudaSuccess) return (unsigned)std::max(cap, 1);
+  int64_t resident = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(fn, dev);
+    const auto it = cache.find(key);
+    if (it != cache.end()) {
+      resident = it->second;
+    } else {
+      int per_sm = 0, sms = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          per_sm < 1 || sms < 1) {
+        (void)cudaGetLastError();
+        return (unsigned)std::max(cap, 1);
+      }
+      resident = (int64_t)per_sm * sms;
+      cache[key] = resident;
+    }
   }
-  const unsigned g = (unsigned)std::min<int64_t>((int64_t)per_sm * sms, cap);
-  cache[key] = g;
-  return g;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(resident, cap));
 }
-
 
 namespace sellp {
 
