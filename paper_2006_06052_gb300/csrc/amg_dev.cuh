@@ -140,7 +140,7 @@ inline bool use_sell(const HCsr& C, int B, int level_format) {
   const int f = level_format_of(level_format);
   if (B < 1 || C.n == 0 || C.n % B != 0 || f == 2) return false;
   if (f == 3) return true;
-  return sell_padding(C, B) <= 0.10;
+  return sell_padding(C, B) <= 0.10;   // 0.4 measured slower in every form
 }
 
 template <class VT>

@@ -277,6 +277,10 @@ inline int choose_group(int64_t nbr, int64_t nnzb) {
     if (nbr <= 1024 && avg >= 128.0) return 256;
     return 0;
   }
+  // a CTA per row when a warp per row leaves the GPU mostly idle and each
+  // row still has two chunks for every lane (C2's 86-row level-2
+  // restriction: 11 CTAs at a warp per row)
+  if (nbr * 32 < LANES_TARGET && chunks >= 512) return 256;
   if (chunks <= 48) return 8;
   if (chunks <= 96) return 16;
   if (chunks <= 768 || nbr > 4096) return 32;

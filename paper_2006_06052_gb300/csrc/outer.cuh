@@ -256,9 +256,13 @@ static __global__ void k_check_outside(int64_t nvals, const unsigned* __restrict
 // p = r + beta (p - omega v), beta = (rho / rho_old) (alpha / omega); p = r on the first step.
 static __global__ void k_bicg_p(int64_t n, const double* __restrict__ r, const double* __restrict__ v,
                          double* __restrict__ p, const double* __restrict__ sc) {
+  // the two FP64 divisions once per CTA, not once per thread
+  __shared__ double sbeta;
   const bool first = sc[S_FIRST] != 0.0;
   const double omega = sc[S_OMEGA];
-  const double beta = first ? 0.0 : (sc[S_RHO] / sc[S_RHO_OLD]) * (sc[S_ALPHA] / omega);
+  if (threadIdx.x == 0) sbeta = first ? 0.0 : (sc[S_RHO] / sc[S_RHO_OLD]) * (sc[S_ALPHA] / omega);
+  __syncthreads();
+  const double beta = sbeta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = first ? r[i] : r[i] + beta * (p[i] - omega * v[i]);
