@@ -453,9 +453,11 @@ def main():
     # profiles/launches_c2_fp64_solve.txt): the outer SpMV as run, timed with
     # CUDA events on the solve's stream right after the timed region
     kform, kstored = gb.outer_format(H)
-    kname = {"block": "k_outer_n", "csr": "k_outer_csr"}[kform]
+    kname = {"block": "k_outer_n", "csr": "k_outer_csr", "sliced": "k_outer_sell"}[kform]
     kdesc = {"block": "as %dx%d blocks" % (B, B),
-             "csr": "as scalar CSR of its %d nonzeros" % nnz_true}[kform]
+             "csr": "as scalar CSR of its %d nonzeros" % nnz_true,
+             "sliced": "as its %d nonzeros in uniform 32-node component slices (%d stored "
+                       "entries, no column indices)" % (nnz_true, kstored)}[kform]
     roofline = {"bound": "hbm", "achieved": csr_gbs, "peak": peak, "unit": "GB/s",
                 "frac": csr_gbs / peak, "traffic": profiled_traffic(kname, spec["system"]),
                 "kernel": "%s (FP64 SpMV of K %s)" % (kname, kdesc),

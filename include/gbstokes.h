@@ -215,10 +215,12 @@ gbs_status gbs_precond_bytes(const gbs_hierarchy* h, double* bytes_per_apply);
 
 /* Layout the FP64 outer SpMV of K runs in now (no counterpart in the
  * paper; the library's per-operator format choice): *format = 0 block
- * CSR, 1 scalar CSR of K's build-time nonzeros.  *stored: value entries
- * the kernel streams (stored block values or nonzeros).  Host only;
- * reflects a pending fall-back to blocks only after the next solve or
- * spmv. */
+ * CSR, 1 scalar CSR of K's build-time nonzeros, 2 those nonzeros in
+ * 32-node component slices (when at least 90% of the slices share their
+ * rows' column offsets, as on a stencil).  *stored: value entries the
+ * kernel streams (stored block values, nonzeros, or slice entries with
+ * padding).  Host only; reflects a pending fall-back to blocks only after
+ * the next solve or spmv. */
 gbs_status gbs_outer_format(const gbs_hierarchy* h, int32_t* format, int64_t* stored);
 
 /* Copy level l (0 = finest) of AMG `which` to host arrays.  part: 0 = A,

@@ -364,7 +364,7 @@ def precond_bytes(H: Hierarchy) -> float:
     return v.value
 
 
-OUTER_FORMATS = ("block", "csr")
+OUTER_FORMATS = ("block", "csr", "sliced")
 
 
 def outer_format(H: Hierarchy):

@@ -155,6 +155,13 @@ DevSell<VT> upload_sell(Arena& ar, const HSell& S, double* err, cudaStream_t s,
   keep.push_back(cast_vec<VT>(S.val));
   d.val = ar.upload(keep.back().data(), keep.back().size(), s);
   d.err = err;
+  d.cinfo = ar.upload(S.cinfo.data(), S.cinfo.size(), s);
+  if (!S.uoff.empty()) {
+    std::vector<int2> ui(S.uoff.size());
+    for (size_t k = 0; k < ui.size(); ++k) ui[k] = make_int2(S.uoff[k], (int)S.umask[k]);
+    d.uinfo = ar.upload(ui.data(), ui.size(), s);
+    GBS_CUDA(cudaStreamSynchronize(s));   // ui dies here
+  }
   return d;
 }
 

@@ -39,7 +39,9 @@ struct Handle {
   // K as scalar CSR of its build-time nonzeros (per-level format choice);
   // the block form stays the source of truth for updates and K^T
   DevCsr<double> Kc;
+  DevSell<double> Ks;            // the same nonzeros in uniform 32-node slices (k_sell)
   bool k_csr = false;
+  bool k_sell = false;
   bool k_check_pending = false;
   int* kmap = nullptr;          // CSR entry -> flat block-value index
   int64_t kmap_n = 0;
@@ -195,14 +197,35 @@ void alloc_work(Handle& h, cudaStream_t s) {
             if (h.Kh.val[flat] != 0.0) map.push_back((int32_t)flat);
             else zero[flat >> 5] |= 1u << (flat & 31);
           }
-    h.Kc.n = c.n;
-    h.Kc.rp = a.upload(c.ptr.data(), c.ptr.size(), s);
-    h.Kc.col = a.upload(c.col.data(), c.col.size(), s);
-    h.kcval = a.upload(c.val.data(), c.val.size(), s);
-    h.Kc.val = h.kcval;
-    h.Kc.S = csr_split(c.n, (int64_t)c.col.size());
-    h.kmap = a.upload(map.data(), map.size(), s);
-    h.kmap_n = (int64_t)map.size();
+    HSell S;
+    bool sliced = false;
+    if (use_sell(c, h.B, h.prm.level_format)) {
+      S = to_sell(c, h.B);
+      int64_t uni = 0;
+      for (int32_t ci : S.cinfo) uni += ci < 0;
+      // only a stencil K gains: its slices need no column loads
+      sliced = level_format_of(h.prm.level_format) == 3 || uni * 10 >= (int64_t)S.nslices * 9;
+    }
+    if (sliced) {
+      std::vector<int32_t> smap(S.src.size());
+      for (size_t e = 0; e < S.src.size(); ++e) smap[e] = S.src[e] >= 0 ? map[S.src[e]] : -1;
+      std::vector<std::vector<double>> keep;
+      h.Ks = upload_sell<double>(a, S, h.sc + S_ERR, s, keep);
+      h.kcval = const_cast<double*>(h.Ks.val);
+      h.kmap = a.upload(smap.data(), smap.size(), s);
+      h.kmap_n = (int64_t)smap.size();
+      h.k_sell = true;
+      GBS_CUDA(cudaStreamSynchronize(s));   // host staging dies here
+    } else {
+      h.Kc.n = c.n;
+      h.Kc.rp = a.upload(c.ptr.data(), c.ptr.size(), s);
+      h.Kc.col = a.upload(c.col.data(), c.col.size(), s);
+      h.kcval = a.upload(c.val.data(), c.val.size(), s);
+      h.Kc.val = h.kcval;
+      h.Kc.S = csr_split(c.n, (int64_t)c.col.size());
+      h.kmap = a.upload(map.data(), map.size(), s);
+      h.kmap_n = (int64_t)map.size();
+    }
     h.kzero = a.upload(zero.data(), zero.size(), s);
     h.kflag = a.alloc<int>(1);
     GBS_CUDA(cudaMemsetAsync(h.kflag, 0, sizeof(int), s));
@@ -289,6 +312,16 @@ void outer_csr(const Handle& h, const double* x, const double* f, double* y, con
 
 void outer(const Handle& h, bool tr, int mode, const double* x, const double* f, double* y,
            const double* w0, int self_dot, int slot, int op, bool reduce, cudaStream_t s) {
+  if (!tr && h.k_csr && h.k_sell) {
+    if (mode == SPMV_RESID)
+      launch_resident(k_outer_sell<SPMV_RESID>, RED_BLOCKS, s, h.Ks, x, f, y, w0, self_dot, h.red,
+                      slot, op, (int)reduce);
+    else
+      launch_resident(k_outer_sell<SPMV_SET>, RED_BLOCKS, s, h.Ks, x, f, y, w0, self_dot, h.red,
+                      slot, op, (int)reduce);
+    GBS_LAUNCH_CHECK();
+    return;
+  }
   if (!tr && h.k_csr) {
     if (mode == SPMV_RESID) outer_csr<SPMV_RESID>(h, x, f, y, w0, self_dot, slot, op, reduce, s);
     else outer_csr<SPMV_SET>(h, x, f, y, w0, self_dot, slot, op, reduce, s);
@@ -1048,7 +1081,10 @@ gbs_status gbs_update_values(gbs_hierarchy* hh, const double* vals, void* stream
     GBS_CUDA(cudaMemcpyAsync(h.Kval, vals, sizeof(double) * h.Kh.val.size(),
                              cudaMemcpyDeviceToDevice, s));
     if (h.k_csr) {
-      k_gather_vals<<<vgrid((int64_t)h.Kh.val.size()), 256, 0, s>>>(h.kmap_n, h.kmap, h.Kval, h.kcval);
+      if (h.k_sell)
+        k_gather_sell<<<vgrid(h.kmap_n), 256, 0, s>>>(h.kmap_n, h.kmap, h.Kval, h.kcval);
+      else
+        k_gather_vals<<<vgrid((int64_t)h.Kh.val.size()), 256, 0, s>>>(h.kmap_n, h.kmap, h.Kval, h.kcval);
       GBS_LAUNCH_CHECK();
       k_check_outside<<<vgrid((int64_t)h.Kh.val.size()), 256, 0, s>>>((int64_t)h.Kh.val.size(), h.kzero,
                                                                       h.Kval, h.kflag);
@@ -1116,7 +1152,7 @@ gbs_status gbs_outer_format(const gbs_hierarchy* hh, int32_t* format, int64_t* s
     if (!hh || !format || !stored) throw SetupError{"null argument"};
     const Handle& h = hh->h;
     if (h.k_csr) {
-      *format = 1;
+      *format = h.k_sell ? 2 : 1;
       *stored = h.kmap_n;
     } else {
       *format = 0;

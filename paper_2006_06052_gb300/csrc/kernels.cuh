@@ -55,6 +55,10 @@ struct DevSell {
   const int* col = nullptr;
   const VT* val = nullptr;
   double* err = nullptr;      // set to 1.0 by a kernel whose pipeline wait timed out
+  // uniform slices (HSell): cinfo[q] < 0, and entry k of lane i sits at
+  // column row_i + uinfo[-1 - cinfo[q] + k].x when bit i of .y is set
+  const int* cinfo = nullptr;
+  const int2* uinfo = nullptr;
 };
 
 // Lanes per scalar CSR row.  Short rows keep one lane per row: that lane

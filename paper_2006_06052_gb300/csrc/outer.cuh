@@ -237,6 +237,42 @@ __global__ void __launch_bounds__(RED_THREADS, 4)
   if (reduce) grid_reduce<2>(d, R, slot, op);
 }
 
+// y = K x (RESID: y = f - K x) with K in 32-node component slices, one
+// warp per slice (grid-stride), direct loads (sell.cuh); dots as k_outer.
+// On a stencil operator every slice is uniform: no column loads, and the
+// gather address comes from the row index.
+template <int MODE>
+__global__ void __launch_bounds__(RED_THREADS, 4)
+    k_outer_sell(DevSell<double> K, const double* __restrict__ x, const double* __restrict__ f,
+                 double* __restrict__ y, const double* __restrict__ w0, int self_dot, Red R,
+                 int slot, int op, int reduce) {
+  double d[2] = {0.0, 0.0};
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < K.nslices; q += nw) {
+    const int64_t g = q / K.B;
+    const int64_t row = (g * 32 + lane) * K.B + (q - g * K.B);
+    const double acc = sell_row_dot_direct<double, double, double>(K, x, (int)q, lane, row);
+    if (row < K.n) {
+      const double val = MODE == SPMV_RESID ? f[row] - acc : acc;
+      y[row] = val;
+      if (w0) d[0] += val * w0[row];
+      if (self_dot) d[1] += val * val;
+    }
+  }
+  if (reduce) grid_reduce<2>(d, R, slot, op);
+}
+
+// Sliced values of K from its block values (map -1: padding).
+static __global__ void k_gather_sell(int64_t n, const int* __restrict__ map,
+                                     const double* __restrict__ bval, double* __restrict__ sval) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int m = map[i];
+    sval[i] = m >= 0 ? bval[m] : 0.0;
+  }
+}
+
 // CSR values of K from its block values (after gbs_update_values).
 static __global__ void k_gather_vals(int64_t nnz, const int* __restrict__ map,
                                      const double* __restrict__ bval, double* __restrict__ cval) {

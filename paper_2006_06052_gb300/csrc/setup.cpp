@@ -534,26 +534,50 @@ HCsr to_scalar_csr(const HBsr& A) {
 }
 
 namespace {
-// Column widths of the slices of the sliced form.
-std::vector<int32_t> sell_widths(const HCsr& C, int B) {
+// Layout of each slice of the sliced form: its width, and for a uniform
+// slice the sorted union of its rows' column offsets (col - row).  A slice
+// is uniform when that union is at most an eighth wider than its longest
+// row (one more column at least); its entry k then sits at column
+// row + union[k] in every lane.
+struct SellPlan {
+  std::vector<int32_t> width;
+  std::vector<std::vector<int32_t>> uni;   // empty: explicit slice
+};
+SellPlan sell_plan(const HCsr& C, int B) {
   const int nn = C.n / B;
   const int ng = (nn + 31) / 32;
-  std::vector<int32_t> w((size_t)ng * B, 0);
-  for (int node = 0; node < nn; ++node)
+  SellPlan P;
+  P.width.assign((size_t)ng * B, 0);
+  P.uni.assign((size_t)ng * B, {});
+  std::vector<int32_t> offs;
+  for (int g = 0; g < ng; ++g)
     for (int c = 0; c < B; ++c) {
-      const int row = node * B + c;
-      const int len = C.ptr[row + 1] - C.ptr[row];
-      int32_t& q = w[(size_t)(node / 32) * B + c];
-      q = std::max(q, len);
+      const size_t q = (size_t)g * B + c;
+      int wmax = 0;
+      offs.clear();
+      for (int node = g * 32; node < std::min(nn, g * 32 + 32); ++node) {
+        const int row = node * B + c;
+        wmax = std::max(wmax, C.ptr[row + 1] - C.ptr[row]);
+        for (int k = C.ptr[row]; k < C.ptr[row + 1]; ++k) offs.push_back(C.col[k] - row);
+      }
+      std::sort(offs.begin(), offs.end());
+      offs.erase(std::unique(offs.begin(), offs.end()), offs.end());
+      const int wu = (int)offs.size();
+      if (wmax > 0 && wu <= wmax + std::max(1, wmax / 8)) {
+        P.width[q] = wu;
+        P.uni[q] = offs;
+      } else {
+        P.width[q] = wmax;
+      }
     }
-  return w;
+  return P;
 }
 }  // namespace
 
 double sell_padding(const HCsr& C, int B) {
   if (B < 1 || C.n % B != 0 || C.col.empty()) return 0.0;
   int64_t slots = 0;
-  for (int32_t w : sell_widths(C, B)) slots += (int64_t)w * 32;
+  for (int32_t w : sell_plan(C, B).width) slots += (int64_t)w * 32;
   return (double)slots / (double)C.col.size() - 1.0;
 }
 
@@ -562,12 +586,18 @@ HSell to_sell(const HCsr& C, int B) {
   HSell S;
   S.n = C.n;
   S.B = B;
-  const std::vector<int32_t> w = sell_widths(C, B);
-  S.nslices = (int)w.size();
+  const SellPlan P = sell_plan(C, B);
+  S.nslices = (int)P.width.size();
   S.off.assign(S.nslices + 1, 0);
+  S.cinfo.assign(S.nslices, 0);
   for (int q = 0; q < S.nslices; ++q) {
-    if ((int64_t)S.off[q] + w[q] > INT32_MAX / 32) throw SetupError{"sliced CSR too large"};
-    S.off[q + 1] = S.off[q] + w[q];
+    if ((int64_t)S.off[q] + P.width[q] > INT32_MAX / 32) throw SetupError{"sliced CSR too large"};
+    S.off[q + 1] = S.off[q] + P.width[q];
+    if (!P.uni[q].empty()) {
+      S.cinfo[q] = -1 - (int32_t)S.uoff.size();
+      S.uoff.insert(S.uoff.end(), P.uni[q].begin(), P.uni[q].end());
+      S.umask.insert(S.umask.end(), P.uni[q].size(), 0u);
+    }
   }
   const size_t slots = (size_t)S.off[S.nslices] * 32;
   S.col.assign(slots, -1);
@@ -578,8 +608,16 @@ HSell to_sell(const HCsr& C, int B) {
     for (int c = 0; c < B; ++c) {
       const int row = node * B + c;
       const int q = (node / 32) * B + c, lane = node % 32;
+      const std::vector<int32_t>& u = P.uni[q];
+      size_t kk = 0;   // position in the union (uniform slices)
       for (int k = C.ptr[row]; k < C.ptr[row + 1]; ++k) {
-        const size_t e = ((size_t)S.off[q] + (k - C.ptr[row])) * 32 + lane;
+        size_t pos = (size_t)(k - C.ptr[row]);
+        if (!u.empty()) {
+          while (u[kk] != C.col[k] - row) ++kk;
+          pos = kk;
+          S.umask[(size_t)(-1 - S.cinfo[q]) + kk] |= 1u << lane;
+        }
+        const size_t e = ((size_t)S.off[q] + pos) * 32 + lane;
         S.col[e] = C.col[k];
         S.val[e] = C.val[k];
         S.src[e] = k;

@@ -102,12 +102,23 @@ double block_fill(const HBsr& A);
 // slice's longest row with column -1 (value 0).  Rows of one component have
 // equal lengths away from boundaries, so a warp walks its slice with every
 // lane busy and each load instruction reads one contiguous run.
+//
+// A slice whose rows share their column offsets (col - row) -- a stencil
+// level, where a slice's rows differ only by missing entries at the
+// boundary -- is "uniform": the union of its rows' offsets is at most an
+// eighth wider than its longest row, entry k of every lane sits at column
+// row + uoff[k], and bit lane of umask[k] says whether that lane has it.
+// The kernels then need no column loads for it: the gather address comes
+// from the row index, not from memory.
 struct HSell {
   int n = 0, B = 1, nslices = 0;
   std::vector<int32_t> off;   // nslices + 1, in columns of 32 entries
   std::vector<int32_t> col;   // off[nslices] * 32
   std::vector<double> val;
   std::vector<int64_t> src;   // entry -> index into the CSR arrays, -1 for padding
+  std::vector<int32_t> cinfo; // per slice: 0 explicit, -1 - (first uoff index) uniform
+  std::vector<int32_t> uoff;  // uniform slices: column offset of each slice column
+  std::vector<uint32_t> umask;
 };
 // Stored entries / nonzeros - 1 of the sliced form (B must divide C.n).
 double sell_padding(const HCsr& C, int B);

@@ -52,11 +52,12 @@ def check_spmv(H, A, x, transpose=False):
 
 
 # ------------------------------------------------------------------ SpMV
-@pytest.mark.parametrize("fmt", ["0", "1", "2"])
+@pytest.mark.parametrize("fmt", ["0", "1", "2", "3"])
 @pytest.mark.parametrize("case", ["c1_csr", "c2_bsr4", "vel_bsr3"])
 def test_outer_spmv_and_transpose(case, fmt, monkeypatch):
-    """K in block form (1), as scalar CSR of its nonzeros (2), or as chosen
-    automatically (0)."""
+    """K in block form (1), as scalar CSR of its nonzeros (2), in 32-node
+    component slices (3), or as chosen automatically (0: slices on these
+    stencil systems)."""
     monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
     N = 9   # 729 nodes: a ragged tail for every rows-per-warp grouping
     if case == "c1_csr":
@@ -505,9 +506,11 @@ def test_c5_mixed_adjoint_matches_fp64_adjoint(N):
     assert abs(grads[gb.GBS_BF16][1] - grads[gb.GBS_FP64][1]) <= 1e-4 * grads[gb.GBS_FP64][1]
 
 
-def test_update_values_inside_csr_pattern():
-    """New values on K's build-time nonzero pattern reach the scalar CSR
-    form of K."""
+@pytest.mark.parametrize("fmt", ["2", "3"])
+def test_update_values_inside_csr_pattern(fmt, monkeypatch):
+    """New values on K's build-time nonzero pattern reach the scalar form
+    of K (plain CSR or slices)."""
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
     s = si.make_system("c2", N=7)
     H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, _params(s, relax=gb.GBS_JACOBI))
     gb.solve(H, dev(s.b))
@@ -523,9 +526,12 @@ def test_update_values_inside_csr_pattern():
     assert np.linalg.norm(s.b - K2 @ host(xs)) / np.linalg.norm(s.b) <= 1e-8
 
 
-def test_update_values_outside_csr_pattern_falls_back_to_blocks():
-    """K runs as scalar CSR of its build-time nonzeros; an update that puts
-    a nonzero where a stored block held a zero must still be honoured."""
+@pytest.mark.parametrize("fmt", ["2", "3"])
+def test_update_values_outside_csr_pattern_falls_back_to_blocks(fmt, monkeypatch):
+    """K runs as scalar CSR (or slices) of its build-time nonzeros; an
+    update that puts a nonzero where a stored block held a zero must still
+    be honoured."""
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
     s = si.make_system("c2", N=7)
     H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, _params(s, relax=gb.GBS_JACOBI))
     gb.solve(H, dev(s.b))            # captures the CUDA-graph iteration with K in CSR form
