@@ -12,7 +12,9 @@
 // direct kernels: the gather address is the row plus the column's offset,
 // so the value and the x entry load together.  The staged kernels read
 // the columns from shared memory, which measured faster than offsets for
-// them (C2 BF16 V-cycle 181 us explicit, 201 us with offsets).
+// them, even with the offsets staged beside the values (C2 BF16 V-cycle:
+// 181 us explicit; 190 us with staged offsets; 201 us with offsets from
+// global memory).
 //
 // For the FP32 and BF16 forms those runs stream into shared memory by
 // bulk asynchronous copies (cp.async.bulk, completion counted on an
