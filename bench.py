@@ -74,10 +74,11 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate (nominal): ~2 DFMA per clock per SM 
 
 
 def kernel_source_sha1():
-    """Hash of the sources of the outer SpMV kernel (kernels.cuh + outer.cuh)."""
+    """Hash of the sources of the outer SpMV kernels (kernels.cuh, sell.cuh,
+    outer.cuh)."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("kernels.cuh", "outer.cuh"):
+    for f in ("kernels.cuh", "sell.cuh", "outer.cuh"):
         with open(os.path.join(ROOT, "paper_2006_06052_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -458,8 +459,12 @@ def main():
              "csr": "as scalar CSR of its %d nonzeros" % nnz_true,
              "sliced": "as its %d nonzeros in uniform 32-node component slices (%d stored "
                        "entries, no column indices)" % (nnz_true, kstored)}[kform]
+    traffic = profiled_traffic(kname, spec["system"])
     roofline = {"bound": "hbm", "achieved": csr_gbs, "peak": peak, "unit": "GB/s",
-                "frac": csr_gbs / peak, "traffic": profiled_traffic(kname, spec["system"]),
+                "frac": csr_gbs / peak, "traffic": traffic,
+                # DRAM bytes actually moved (ncu) over the same time: below the
+                # algorithmic figure when the format needs no column indices
+                "traffic_gbs": traffic / (spmv_ms * 1e-3) / 1e9 if traffic else None,
                 "kernel": "%s (FP64 SpMV of K %s)" % (kname, kdesc),
                 "algorithmic_bytes": csr_bytes, "ms": spmv_ms, "peak_kind": peak_kind,
                 "fp64": {"achieved_tflops": 2.0 * nnz_true / (spmv_ms * 1e-3) / 1e12,
