@@ -105,6 +105,49 @@ def profiled_traffic(kernel, workload):
         return None
 
 
+def level1_relax_roofline(gb, H, B, precision, timed, peak, peak_kind):
+    """Roofline of one level-1 relaxation sweep y = x + M (f - A_1 x) (block
+    form when the level's blocks are more than half nonzero): FP64 is bound
+    by the FP64 pipe (B*B FMAs a stored block), the FP32/BF16 forms by HBM."""
+    import torch
+    info = gb.hierarchy_info(H)
+    if info["nlevels"] < 3:
+        return None
+    nbr, nnzb = info["n_brows"][1], info["nnzb"][1]
+    vals = gb.export_level(H, 0, 1, 0)[2]
+    nnz = int(np.count_nonzero(vals))
+    block = nnz > 0.5 * vals.size
+    n = nbr * B
+    sv, sx = {0: (8, 8), 1: (4, 4), 2: (2, 4)}[precision]
+    dt = torch.float64 if precision == 0 else torch.float32
+    g = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.randn(n, dtype=dt, device="cuda", generator=g)
+    f = torch.randn(n, dtype=dt, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    ms = timed(lambda: gb.level_apply(H, 0, 1, 1, x, f, y))
+    a_bytes = nnzb * (B * B * sv + 4) + 4 * (nbr + 1) if block else nnz * (sv + 4) + 4 * (n + 1)
+    nbytes = a_bytes + nbr * B * B * sv + 3 * n * sx
+    flops = 2.0 * (nnzb * B * B if block else nnz) + 2.0 * n * B + n
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    tflops = flops / (ms * 1e-3) / 1e12
+    kname = ("k_relax" if block else "k_csr_relax") + (" (FP64, %dx%d blocks)" % (B, B) if block
+                                                     else " (scalar CSR)")
+    desc = ("%s: level-1 relaxation sweep y = x + M (f - A_1 x), %d block rows, %d stored blocks"
+            % (kname, nbr, nnzb))
+    traffic = profiled_traffic("k_relax_level1", "c2") if precision == 0 else None
+    hbm = {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+           "algorithmic_bytes": nbytes, "peak_kind": peak_kind}
+    if precision == 0:
+        return {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": desc,
+                "ms": ms, "algorithmic_flops": flops,
+                "peak_kind": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop",
+                "hbm": hbm}
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "traffic": traffic, "kernel": desc, "ms": ms, "algorithmic_bytes": nbytes,
+            "peak_kind": peak_kind}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -450,9 +493,8 @@ def main():
                 "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "algorithmic_bytes": spmv_bytes, "peak_kind": peak_kind},
                 "traffic": profiled_traffic("k_outer_n", spec["system"])}
-    # the dominant kernel of the solve (largest share of the ncu launch list,
-    # profiles/launches_c2_fp64_solve.txt): the outer SpMV as run, timed with
-    # CUDA events on the solve's stream right after the timed region
+    # the outer SpMV of K as the solve runs it, timed with CUDA events on the
+    # solve's stream right after the timed region
     kform, kstored = gb.outer_format(H)
     kname = {"block": "k_outer_n", "csr": "k_outer_csr", "sliced": "k_outer_sell"}[kform]
     kdesc = {"block": "as %dx%d blocks" % (B, B),
@@ -460,15 +502,22 @@ def main():
              "sliced": "as its %d nonzeros in uniform 32-node component slices (%d stored "
                        "entries, no column indices)" % (nnz_true, kstored)}[kform]
     traffic = profiled_traffic(kname, spec["system"])
-    roofline = {"bound": "hbm", "achieved": csr_gbs, "peak": peak, "unit": "GB/s",
-                "frac": csr_gbs / peak, "traffic": traffic,
-                # DRAM bytes actually moved (ncu) over the same time: below the
-                # algorithmic figure when the format needs no column indices
-                "traffic_gbs": traffic / (spmv_ms * 1e-3) / 1e9 if traffic else None,
-                "kernel": "%s (FP64 SpMV of K %s)" % (kname, kdesc),
-                "algorithmic_bytes": csr_bytes, "ms": spmv_ms, "peak_kind": peak_kind,
-                "fp64": {"achieved_tflops": 2.0 * nnz_true / (spmv_ms * 1e-3) / 1e12,
-                         "peak_tflops": FP64_PEAK_TFLOPS}}
+    outer_spmv = {"bound": "hbm", "achieved": csr_gbs, "peak": peak, "unit": "GB/s",
+                  "frac": csr_gbs / peak, "traffic": traffic,
+                  # DRAM bytes actually moved (ncu) over the same time: below the
+                  # algorithmic figure when the format needs no column indices
+                  "traffic_gbs": traffic / (spmv_ms * 1e-3) / 1e9 if traffic else None,
+                  "kernel": "%s (FP64 SpMV of K %s)" % (kname, kdesc),
+                  "algorithmic_bytes": csr_bytes, "ms": spmv_ms, "peak_kind": peak_kind,
+                  "fp64": {"achieved_tflops": 2.0 * nnz_true / (spmv_ms * 1e-3) / 1e12,
+                           "peak_tflops": FP64_PEAK_TFLOPS}}
+    roofline = outer_spmv
+    # the dominant kernel of the C2 solve by ncu launch-list share
+    # (profiles/launches_c2_fp64_solve.txt): the level-1 relaxation sweep,
+    # timed through gbs_level_apply exactly as the V-cycle launches it
+    if spec["system"] == "c2":
+        roofline = level1_relax_roofline(gb, H, B, spec["precision"], timed, peak, peak_kind) \
+            or outer_spmv
     # the V-cycle as a whole (monolithic AMG only)
     vcycle = None
     if spec["system"] != "c3":
@@ -501,6 +550,7 @@ def main():
                 "d2h_bytes_per_step": int(x.numel() * 8)},
         "gpu_launches": int(launches),
         "roofline": roofline,
+        "outer_spmv": outer_spmv,
         "bsr_spmv": bsr_spmv,
         "vcycle": vcycle,
         "clocks": clocks,

@@ -223,6 +223,18 @@ gbs_status gbs_precond_bytes(const gbs_hierarchy* h, double* bytes_per_apply);
  * the next solve or spmv. */
 gbs_status gbs_outer_format(const gbs_hierarchy* h, int32_t* format, int64_t* stored);
 
+/* One operation on level `level` (below the coarsest) of AMG `which` (0
+ * monolithic / velocity, 1 pressure), launched exactly as the V-cycle
+ * launches it (no counterpart in the paper; for measurement and tests):
+ * op 0: y = f - A_l x (the residual of Section 2.3's primitives);
+ * op 1: one relaxation sweep y = x + S (f - A_l x), S the level's SPAI0,
+ * Jacobi or ILUT smoother.  x, f, y: device vectors of the level's scalar
+ * size in the hierarchy's vector type (double for GBS_FP64, float for the
+ * FP32/BF16 forms), 16-byte aligned; y aliases neither.  Asynchronous on
+ * stream. */
+gbs_status gbs_level_apply(gbs_hierarchy* h, int32_t which, int32_t level, int32_t op,
+                           const void* x_dev, const void* f_dev, void* y_dev, void* stream);
+
 /* Copy level l (0 = finest) of AMG `which` to host arrays.  part: 0 = A,
  * 1 = P, 2 = R, 3 = smoother blocks M (row_ptr/col_idx untouched),
  * 4 = aggregate ids (written to col_idx, n_brows entries), 5 = dense

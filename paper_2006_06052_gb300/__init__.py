@@ -40,7 +40,7 @@ EXPORTED = [
     "gbs_sampled_outer", "gbs_update_values", "gbs_spmv", "gbs_apply_precond",
     "gbs_hierarchy_info", "gbs_export_level", "gbs_import_hierarchy", "gbs_destroy",
     "gbs_last_error", "gbs_kernel_launches", "gbs_spmv_dots_noalloc", "gbs_precond_bytes",
-    "gbs_outer_format",
+    "gbs_outer_format", "gbs_level_apply",
 ]
 
 
@@ -128,6 +128,7 @@ def load_library():
         "gbs_destroy": [P],
         "gbs_precond_bytes": [P, c.POINTER(c.c_double)],
         "gbs_outer_format": [P, c.POINTER(c.c_int32), c.POINTER(c.c_int64)],
+        "gbs_level_apply": [P, c.c_int32, c.c_int32, c.c_int32, P, P, P, P],
         "gbs_spmv_dots_noalloc": [c.c_int32, c.c_int32, c.c_int32, c.c_int64, P, P, P, P, P, P,
                                   P, P],
     }
@@ -362,6 +363,24 @@ def precond_bytes(H: Hierarchy) -> float:
     v = ctypes.c_double()
     _check(load_library().gbs_precond_bytes(H.handle, ctypes.byref(v)))
     return v.value
+
+
+def level_apply(H: Hierarchy, which: int, level: int, op: int, x, f, y=None, stream=None):
+    """One level operation as the V-cycle runs it: op 0 y = f - A_l x, op 1 one
+    relaxation sweep y = x + S (f - A_l x).  x, f, y: CUDA tensors of the
+    level's scalar size, float64 for GBS_FP64 hierarchies, float32 otherwise."""
+    import torch
+    want = torch.float64 if H.params.precision == GBS_FP64 else torch.float32
+    for name, t in (("x", x), ("f", f)):
+        if not (t.is_cuda and t.dtype == want and t.is_contiguous()):
+            raise GbsError(-1, "%s must be a contiguous CUDA %s tensor" % (name, want))
+    if y is None:
+        y = torch.empty_like(x)
+    if y.dtype != want or y.numel() != x.numel() or f.numel() != x.numel():
+        raise GbsError(-1, "x, f, y must have the same size and dtype")
+    _check(load_library().gbs_level_apply(H.handle, which, level, op, x.data_ptr(), f.data_ptr(),
+                                          y.data_ptr(), _stream_ptr(stream)))
+    return y
 
 
 OUTER_FORMATS = ("block", "csr", "sliced")

@@ -487,6 +487,34 @@ struct DevAmg {
   }
 
   // out = V(f) at level l; f and out are ST vectors of that level's size.
+  // r = f - A_l x (A^T when TR)
+  template <bool TR>
+  void resid(Lev& L, const ST* x, const ST* f, ST* r, cudaStream_t s) {
+    const bool acsr = L.a_csr && !TR;   // A^T goes through the block form's transpose map
+    if (acsr && L.a_sell) sell_spmv<SPMV_RESID, VT, ST, ST, AT>(L.As, x, f, r, s);
+    else if (acsr) csr_spmv<SPMV_RESID, VT, ST, ST, AT>(L.Ac, x, f, r, s);
+    else spmv<TR, SPMV_RESID, VT, ST, ST, AT>(B, L.A, x, f, r, s);
+  }
+
+  // One relaxation sweep xout = xin + S (f - A_l xin) (S^T, A^T when TR).
+  template <bool TR>
+  void sweep(Lev& L, const ST* f, const ST* xin, ST* xout, cudaStream_t s) {
+    const bool acsr = L.a_csr && !TR;
+    if (L.ilu) {   // xout = xin + omega S (f - A xin)
+      resid<TR>(L, xin, f, L.r, s);
+      const ST* z = ilu_apply<TR>(L, L.r, s);
+      k_vaxpy<ST><<<grid_for(L.n), 256, 0, s>>>(L.n, xin, (ST)ilu_omega, z, xout);
+      GBS_LAUNCH_CHECK();
+    } else if (acsr && L.a_sell) {
+      sell_relax<VT, ST, AT>(B, L.As, L.M, f, xin, xout, s);
+    } else if (acsr) {
+      csr_relax<VT, ST, AT>(B, L.Ac, L.M, f, xin, xout, s);
+    } else {
+      relax<TR, VT, ST, AT>(B, L.A, L.M, f, xin, xout, s);
+    }
+  }
+
+  // out = V(f) at level l; f and out are ST vectors of that level's size.
   template <bool TR>
   void cycle(size_t l, const ST* f, ST* out, cudaStream_t s) {
     if (l + 1 == lev.size()) {
@@ -501,42 +529,22 @@ struct DevAmg {
     const int post = TR ? npre : npost;
     ST* x = L.x;
     ST* xt = L.xt;
-    const bool acsr = L.a_csr && !TR;   // A^T goes through the block form's transpose map
-    const unsigned gv = grid_for(L.n);
-    auto sweep = [&](const ST* xin, ST* xout) {
-      if (L.ilu) {   // xout = xin + omega S (f - A xin)
-        if (acsr && L.a_sell) sell_spmv<SPMV_RESID, VT, ST, ST, AT>(L.As, xin, f, L.r, s);
-        else if (acsr) csr_spmv<SPMV_RESID, VT, ST, ST, AT>(L.Ac, xin, f, L.r, s);
-        else spmv<TR, SPMV_RESID, VT, ST, ST, AT>(B, L.A, xin, f, L.r, s);
-        const ST* z = ilu_apply<TR>(L, L.r, s);
-        k_vaxpy<ST><<<gv, 256, 0, s>>>(L.n, xin, (ST)ilu_omega, z, xout);
-        GBS_LAUNCH_CHECK();
-      } else if (acsr && L.a_sell) {
-        sell_relax<VT, ST, AT>(B, L.As, L.M, f, xin, xout, s);
-      } else if (acsr) {
-        csr_relax<VT, ST, AT>(B, L.Ac, L.M, f, xin, xout, s);
-      } else {
-        relax<TR, VT, ST, AT>(B, L.A, L.M, f, xin, xout, s);
-      }
-    };
     if (pre >= 1) {
       if (L.ilu) {
         const ST* z = ilu_apply<TR>(L, f, s);
-        k_vaxpy<ST><<<gv, 256, 0, s>>>(L.n, (const ST*)nullptr, (ST)ilu_omega, z, x);
+        k_vaxpy<ST><<<grid_for(L.n), 256, 0, s>>>(L.n, (const ST*)nullptr, (ST)ilu_omega, z, x);
         GBS_LAUNCH_CHECK();
       } else {
         mapply<TR, VT, ST, AT>(B, nb, L.M, f, x, s);
       }
       for (int it = 1; it < pre; ++it) {
-        sweep(x, xt);
+        sweep<TR>(L, f, x, xt, s);
         std::swap(x, xt);
       }
     } else {
       GBS_CUDA(cudaMemsetAsync(x, 0, sizeof(ST) * L.n, s));
     }
-    if (acsr && L.a_sell) sell_spmv<SPMV_RESID, VT, ST, ST, AT>(L.As, x, f, L.r, s);
-    else if (acsr) csr_spmv<SPMV_RESID, VT, ST, ST, AT>(L.Ac, x, f, L.r, s);
-    else spmv<TR, SPMV_RESID, VT, ST, ST, AT>(B, L.A, x, f, L.r, s);
+    resid<TR>(L, x, f, L.r, s);
     Lev& Cn = lev[l + 1];
     const ST* none = nullptr;
     if (L.r_sell) sell_spmv<SPMV_SET, VT, ST, ST, AT>(L.Rs, L.r, none, Cn.f, s);
@@ -548,9 +556,18 @@ struct DevAmg {
     else spmv<false, SPMV_ADD, VT, ST, ST, AT>(B, L.Pm, Cn.e, none, x, s);
     for (int it = 0; it < post; ++it) {
       ST* dst = (it + 1 == post) ? out : xt;
-      sweep(x, dst);
+      sweep<TR>(L, f, x, dst, s);
       std::swap(x, xt);
     }
+  }
+
+  // One level operation as the V-cycle runs it (measurement and tests):
+  // op 0: y = f - A_l x; op 1: one relaxation sweep y = x + S (f - A_l x).
+  void level_op(size_t l, int op, const ST* x, const ST* f, ST* y, cudaStream_t s) {
+    if (l + 1 >= lev.size()) throw SetupError{"level_op: the coarsest level has no smoother"};
+    if (op == 0) resid<false>(lev[l], x, f, y, s);
+    else if (op == 1) sweep<false>(lev[l], f, x, y, s);
+    else throw SetupError{"level_op: op must be 0 (residual) or 1 (relaxation sweep)"};
   }
 
   void vcycle(const ST* f, ST* out, bool tr, cudaStream_t s) {
@@ -618,6 +635,13 @@ struct AmgPrecond final : DevPrecond {
     }
   }
   int64_t bytes() const override { return amg.ar.bytes + ar.bytes; }
+  void level_op(int which, int l, int op, const void* x, const void* f, void* y,
+                cudaStream_t s) override {
+    if (which != 0) throw SetupError{"level_op: the monolithic AMG is hierarchy 0"};
+    amg.level_op((size_t)l, op, static_cast<const ST*>(x), static_cast<const ST*>(f),
+                 static_cast<ST*>(y), s);
+  }
+  int vector_bytes() const override { return (int)sizeof(ST); }
   int nlevels(int which) const override { return which == 0 ? (int)amg.lev.size() : 0; }
   int64_t level_rows(int, int l) const override { return amg.lev[l].n / amg.B; }
   int64_t level_nnzb(int, int l) const override { return amg.lev[l].nnzb_A; }
@@ -800,6 +824,14 @@ struct SchurPrecond final : DevPrecond {
     }
   }
   int64_t bytes() const override { return A.ar.bytes + S.ar.bytes + ar.bytes; }
+  void level_op(int which, int l, int op, const void* x, const void* f, void* y,
+                cudaStream_t s) override {
+    if (which == 1 && MS) throw SetupError{"level_op: the pressure solve is one sweep (no AMG)"};
+    DevAmg<P>& H = which == 0 ? A : S;
+    H.level_op((size_t)l, op, static_cast<const ST*>(x), static_cast<const ST*>(f),
+               static_cast<ST*>(y), s);
+  }
+  int vector_bytes() const override { return (int)sizeof(ST); }
   int nlevels(int which) const override {
     return which == 0 ? (int)A.lev.size() : (int)S.lev.size();
   }

@@ -1147,6 +1147,24 @@ gbs_status gbs_hierarchy_info(const gbs_hierarchy* hh, int32_t which, int32_t* n
   });
 }
 
+gbs_status gbs_level_apply(gbs_hierarchy* hh, int32_t which, int32_t level, int32_t op,
+                           const void* x, const void* f, void* y, void* stream) {
+  return guarded([&]() -> gbs_status {
+    if (!hh || !x || !f || !y) throw SetupError{"null argument"};
+    Handle& h = hh->h;
+    need_device(h);
+    if (which < 0 || which > 1 || (which == 1 && !h.schur)) throw SetupError{"bad hierarchy id"};
+    if (level < 0 || level + 1 >= h.pc->nlevels(which))
+      throw SetupError{"level must be below the coarsest"};
+    if (x == y || f == y) throw SetupError{"y must not alias x or f"};
+    need_aligned(x, "x");
+    need_aligned(f, "f");
+    need_aligned(y, "y");
+    h.pc->level_op(which, level, op, x, f, y, S(stream));
+    return GBS_OK;
+  });
+}
+
 gbs_status gbs_outer_format(const gbs_hierarchy* hh, int32_t* format, int64_t* stored) {
   return guarded([&]() -> gbs_status {
     if (!hh || !format || !stored) throw SetupError{"null argument"};

@@ -75,6 +75,14 @@ struct DevPrecond {
   virtual int64_t level_nnzb(int which, int l) const = 0;
   // algorithmic bytes moved by one application (from the stored sizes)
   virtual double bytes_per_apply() const = 0;
+  // one level operation of AMG `which` (0 residual, 1 relaxation sweep) on
+  // vectors of the hierarchy's vector type (vector_bytes() wide)
+  virtual void level_op(int which, int l, int op, const void* x, const void* f, void* y,
+                        cudaStream_t s) {
+    (void)which; (void)l; (void)op; (void)x; (void)f; (void)y; (void)s;
+    throw SetupError{"level_op is not available for this preconditioner"};
+  }
+  virtual int vector_bytes() const { return 8; }
 };
 
 struct PrecondOptions {

@@ -681,3 +681,27 @@ def test_schur_ilut_solve_matches_oracle(precision):
     assert info.converged and _true_rel(s, host(x)) <= 1e-8
     if precision == gb.GBS_FP64:
         assert abs(info.iters - io.iters) <= max(1, math.ceil(0.1 * io.iters)), (info.iters, io.iters)
+
+
+# ------------------------------------------------------------------ level ops
+@pytest.mark.parametrize("relax", ["jacobi", "spai0", "ilut"])
+def test_level_apply_matches_oracle(relax):
+    """gbs_level_apply runs one level operation as the V-cycle launches it:
+    the residual and one relaxation sweep of every level below the coarsest
+    match the oracle's."""
+    s = si.make_system("c2", N=9)
+    A = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    Ho = amg.build_hierarchy(A, amg.AmgParams(coarse_enough=50, relax=relax))
+    code = {"jacobi": gb.GBS_JACOBI, "spai0": gb.GBS_SPAI0, "ilut": gb.GBS_ILUT}[relax]
+    H = _import(Ho, 4, relax=code)
+    rng = np.random.default_rng(61)
+    for l, lev in enumerate(Ho.levels):
+        As = lev.A.scipy()
+        n = As.shape[0]
+        x, f = rng.standard_normal(n), rng.standard_normal(n)
+        r = host(gb.level_apply(H, 0, l, 0, dev(x), dev(f)))
+        assert rel_inf(r, f - As @ x) <= 1e-13, ("resid", l)
+        y = host(gb.level_apply(H, 0, l, 1, dev(x), dev(f)))
+        assert rel_inf(y, x + amg.smooth(lev, f - As @ x)) <= 1e-12, ("sweep", l)
+    with pytest.raises(gb.GbsError):
+        gb.level_apply(H, 0, len(Ho.levels), 0, dev(np.zeros(4)), dev(np.zeros(4)))
