@@ -705,3 +705,22 @@ def test_level_apply_matches_oracle(relax):
         assert rel_inf(y, x + amg.smooth(lev, f - As @ x)) <= 1e-12, ("sweep", l)
     with pytest.raises(gb.GbsError):
         gb.level_apply(H, 0, len(Ho.levels), 0, dev(np.zeros(4)), dev(np.zeros(4)))
+
+
+def test_schur_ilut_pressure_amg_matches_oracle():
+    """ILUT relaxation in the pressure AMG on S_hat (relax_p = ILUT) as well
+    as in the velocity AMG: the application (forward and transposed)
+    matches the oracle's, and GMRES(30) converges."""
+    s = si.make_system("c3", N=10)
+    K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    po = amg.AmgParams(coarse_enough=60, relax="ilut")
+    pc = schur.build(K, 3, po, po)
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
+                           _params(s, coarse_enough=60, relax=gb.GBS_ILUT, relax_p=gb.GBS_ILUT))
+    rng = np.random.default_rng(71)
+    for tr in (False, True):
+        r = rng.standard_normal(K.shape[0])
+        z = host(gb.apply_precond(H, dev(r), transpose=tr))
+        assert rel_inf(z, pc.apply(r, transpose=tr)) <= 1e-10, tr
+    x, info = gb.solve(H, dev(s.b))
+    assert info.converged and _true_rel(s, host(x)) <= 1e-8
