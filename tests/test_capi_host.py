@@ -156,6 +156,8 @@ def test_setup_only_handle_refuses_device_calls():
     assert info["bytes"] == 0 and info["nlevels"] >= 1
     # no device form of K exists: the outer SpMV format reads as block
     assert gb.outer_format(H) == ("block", s.data.size)
+    # device calls are refused on a host-only handle (no GPU touched)
+    assert gb.load_library().gbs_level_apply(H.handle, 0, 0, 0, 16, 16, 32, None) == -1
 
 
 def test_host_setup_plain_aggregation_matches_oracle():
