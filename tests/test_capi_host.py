@@ -216,3 +216,13 @@ def test_ilut_parameters_validated():
         _host(s, relax=gb.GBS_ILUT, ilut_omega=0.0)
     with pytest.raises(gb.GbsError):
         _host(s, precond=gb.GBS_PC_SCHUR, schur_p=1, relax_p=gb.GBS_ILUT)
+
+
+def test_params_layout_matches_the_header():
+    """gbs_params_default fills the ctypes mirror: the trailing fields come
+    back with their documented defaults only if every field before them has
+    the C layout."""
+    p = gb.params_default()
+    assert (p.idr_s, p.idr_seed) == (5, 0)
+    assert (p.ilut_p, p.ilut_tau, p.ilut_sweeps, p.ilut_omega) == (2.0, 1e-2, 2, 1.0)
+    assert (p.relax, p.relax_p, p.level_format, p.schur_p, p.schur_order) == (0, 0, 0, 0, 0)
