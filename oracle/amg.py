@@ -47,6 +47,7 @@ import scipy.sparse as sp
 
 from . import ilut as ilut_mod
 from .bsr import Bsr, from_scipy, spmv
+from .precision import round_to
 
 
 @dataclass
@@ -310,3 +311,26 @@ def vcycle_dense(H: Hierarchy, transpose: bool = False) -> np.ndarray:
     n = H.A(0).shape[0]
     cols = [vcycle(H, e, 0, transpose) for e in np.eye(n)]
     return np.array(cols).T
+
+
+def _rounded(A: Bsr, fmt: str) -> Bsr:
+    return Bsr(A.indptr, A.indices, round_to(A.data, fmt), A.n_bcols)
+
+
+def cast_values(H: Hierarchy, fmt: str) -> Hierarchy:
+    """The hierarchy as a mixed-precision form stores it (Section 4's
+    single-precision preconditioner, Listing V4, and its BF16 extension):
+    A_l, P_l, R_l and the smoother blocks M_l rounded to `fmt` ("fp32" or
+    "bf16"), the dense coarse inverse rounded to FP32 in both forms.  The
+    result is an ordinary FP64 hierarchy holding those rounded values, so
+    vcycle() on it differs from the GPU's mixed form only by the GPU's
+    FP32 accumulation.  ILUT levels are not modelled."""
+    levels = []
+    for lev in H.levels:
+        if lev.S is not None:
+            raise ValueError("cast_values: ILUT levels are not modelled")
+        levels.append(Level(A=_rounded(lev.A, fmt), M=round_to(lev.M, fmt),
+                            P=_rounded(lev.P, fmt), R=_rounded(lev.R, fmt), agg=lev.agg))
+    return Hierarchy(levels=levels, A_coarse=_rounded(H.A_coarse, fmt),
+                     Ainv_coarse=round_to(H.Ainv_coarse, "fp32"), params=H.params,
+                     omegas=list(H.omegas))

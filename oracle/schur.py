@@ -27,6 +27,7 @@ import scipy.sparse as sp
 
 from . import amg
 from .bsr import Bsr, from_scipy
+from .precision import round_to
 
 
 @dataclass
@@ -128,3 +129,19 @@ def build(K: Bsr, nvel: int = 3, prmA: amg.AmgParams | None = None,
     prmS = prmS or amg.AmgParams()
     M = amg.spai0(Sh) if pressure == "spai0" else amg.jacobi(Sh, prmS.jacobi_omega)
     return SchurPrecond(S, Sh, HA, None, order, M)
+
+
+def cast_values(pc: SchurPrecond, fmt: str) -> SchurPrecond:
+    """The preconditioner as a mixed-precision form stores it: both inner
+    hierarchies (amg.cast_values), the couplings G and D and the pressure
+    smoother rounded to `fmt`.  C and S_hat enter only through the pressure
+    hierarchy."""
+    S = pc.split
+
+    def rb(A):
+        return Bsr(A.indptr, A.indices, round_to(A.data, fmt), A.n_bcols)
+
+    sp_ = SchurSplit(S.A, rb(S.G), rb(S.D), S.C, S.nvel)
+    return SchurPrecond(sp_, pc.S_hat, amg.cast_values(pc.HA, fmt),
+                        amg.cast_values(pc.HS, fmt) if pc.HS is not None else None,
+                        pc.order, round_to(pc.M_S, fmt) if pc.M_S is not None else None)

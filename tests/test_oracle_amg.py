@@ -243,3 +243,66 @@ def test_plain_aggregation_prolongator_is_tentative():
     for lev in H.levels:
         Pt = amg.tentative_P(lev.agg, lev.P.n_bcols, 4)
         np.testing.assert_array_equal(lev.P.dense(), Pt.dense())
+
+
+# ------------------------------------------------------- level schedule
+def chain8(weak):
+    """8-node scalar chain, diagonal 4; strong pairs (0,1), (2,3), (4,5),
+    (6,7) coupled by -2.5 and the pairs between them by `weak`."""
+    M = 4.0 * np.eye(8)
+    for i in range(7):
+        c = -2.5 if i % 2 == 0 else weak
+        M[i, i + 1] = M[i + 1, i] = c
+    return bsr.from_scipy(sp.csr_matrix(M), 1, 1)
+
+
+def test_level_schedule_hand_computed_three_levels():
+    """The strength threshold is eps at level 0 and eps/2 at level 1
+    (eps_l = eps 0.5^l).  eps = 0.5, plain aggregation (P = P_tent), so the
+    coarse operators are sums of entries.
+
+    Level 0: a coupling c is strong iff c^2 > 0.25 * 4 * 4 = 4.
+      6.25 > 4: strong; 1.5625 <= 4: weak.  Pass 1 gives {0,1} {2,3}
+      {4,5} {6,7}.  (At eps/2 the threshold would be 1 and the weak
+      pairs would be strong.)
+    Level 1: A_1 = P^T A_0 P is tridiagonal with diagonal 4+4-2*2.5 = 3
+      and off-diagonal -1.25.  Threshold 0.25^2 * 3 * 3 = 0.5625 < 1.5625:
+      strong.  (At eps it would be 2.25: every node a singleton.)  Pass 1:
+      root 0 takes {0,1}; node 2 sees aggregated 1; root 3 takes {3,2}.
+    Level 2: A_2 = [[3.5, -1.25], [-1.25, 3.5]] holds 2 unknowns, at most
+      coarse_enough = 2: the coarsest level."""
+    H = amg.build_hierarchy(chain8(-1.25),
+                            amg.AmgParams(eps_strong=0.5, coarse_enough=2, smooth_P=False,
+                                          relax="jacobi"))
+    assert H.nlevels == 3
+    assert H.levels[0].agg.tolist() == [0, 0, 1, 1, 2, 2, 3, 3]
+    assert H.levels[1].agg.tolist() == [0, 0, 1, 1]
+    np.testing.assert_array_equal(H.levels[1].A.dense(),
+                                  [[3, -1.25, 0, 0], [-1.25, 3, -1.25, 0],
+                                   [0, -1.25, 3, -1.25], [0, 0, -1.25, 3]])
+    np.testing.assert_array_equal(H.A_coarse.dense(), [[3.5, -1.25], [-1.25, 3.5]])
+    np.testing.assert_allclose(H.Ainv_coarse, np.linalg.inv([[3.5, -1.25], [-1.25, 3.5]]),
+                               rtol=1e-15)
+
+
+def test_level_schedule_stop_rules():
+    """The three ways coarsening ends, on the same chain.
+    coarse_enough = 1: level 2 (2 unknowns) coarsens once more, eps_2 =
+      0.125: threshold 0.015625 * 3.5^2 < 1.5625, one aggregate, A_3 = [4.5].
+    max_levels = 3 stops after two coarsenings although 2 > coarse_enough.
+    weak = -0.7: level 1's couplings (0.49 <= 0.5625) are all weak, every
+      node is a singleton, aggregation does not shrink the level: stop."""
+    A = chain8(-1.25)
+    H4 = amg.build_hierarchy(A, amg.AmgParams(eps_strong=0.5, coarse_enough=1, smooth_P=False,
+                                              relax="jacobi"))
+    assert H4.nlevels == 4
+    assert H4.levels[2].agg.tolist() == [0, 0]
+    np.testing.assert_array_equal(H4.A_coarse.dense(), [[4.5]])
+    H3 = amg.build_hierarchy(A, amg.AmgParams(eps_strong=0.5, coarse_enough=1, max_levels=3,
+                                              smooth_P=False, relax="jacobi"))
+    assert H3.nlevels == 3 and H3.A_coarse.n_brows == 2
+    H2 = amg.build_hierarchy(chain8(-0.7),
+                             amg.AmgParams(eps_strong=0.5, coarse_enough=1, smooth_P=False,
+                                           relax="jacobi"))
+    assert H2.nlevels == 2 and H2.A_coarse.n_brows == 4
+    assert H2.levels[0].agg.tolist() == [0, 0, 1, 1, 2, 2, 3, 3]
