@@ -261,6 +261,36 @@ gbs_status gbs_import_hierarchy(const gbs_bsr* A, const gbs_bsr* P, const gbs_bs
                                 const gbs_params* params, void* stream,
                                 gbs_hierarchy** out);
 
+/* One AMG hierarchy given level by level, as gbs_import_hierarchy takes
+ * it: A[0..nlev-1], P[0..nlev-2], R[0..nlev-2], M[0..nlev-2] smoother
+ * blocks (double[n_brows_l * bdim^2] each; may be NULL with ILUT
+ * relaxation) and the dense coarse inverse Ainv (double[n_L^2]).  All
+ * host memory, read during the call only. */
+typedef struct {
+  const gbs_bsr* A;
+  const gbs_bsr* P;
+  const gbs_bsr* R;
+  const double* const* M;
+  const double* Ainv;
+  int32_t nlev;
+} gbs_levels;
+
+/* Build a Schur pressure-correction preconditioner (Section 4, Eq.
+ * SchurPC) from caller-supplied inner hierarchies instead of running the
+ * setup.  K: host BSR of the saddle-point system, bdim = nvel + 1, the
+ * pressure unknown last in each block; its couplings G (velocity rows,
+ * pressure column) and D (pressure row, velocity columns) are taken from
+ * K's blocks as stored.  vel: the velocity AMG (bdim = params->nvel, level
+ * 0 the velocity block of K).  pres: the pressure AMG on the operator of
+ * Eq. SchurApprox (bdim 1), used when params->schur_p = 0 (may be NULL
+ * otherwise).  pres_smoother: double[n_brows of K], the diagonal pressure
+ * smoother applied once when params->schur_p = 1 (may be NULL otherwise).
+ * params->precond must be GBS_PC_SCHUR; the other arguments are as in
+ * gbs_build_hierarchy.  Shapes are checked before any device work. */
+gbs_status gbs_import_schur(const gbs_bsr* K, const gbs_levels* vel, const gbs_levels* pres,
+                            const double* pres_smoother, const gbs_params* params,
+                            void* stream, gbs_hierarchy** out);
+
 /* Number of CUDA kernels this library has launched in this process (a
  * replayed CUDA graph counts each of its kernel nodes).  Telemetry only. */
 int64_t gbs_kernel_launches(void);
@@ -283,14 +313,27 @@ int64_t gbs_kernel_launches(void);
  * pointers, caller-owned; vals, x, y, w 16-byte aligned; w must not alias
  * y.  The structure is not validated (it lives on the device).
  * The first call on a device looks up the scratch address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one scratch array, so
+ * (cudaGetSymbolAddress) with that device current and keeps it for the
+ * life of the process; make that first call before any stream capture.
+ * A cudaDeviceReset of that device (which also frees every hierarchy's
+ * device memory) invalidates the kept address: call this entry point no
+ * more in that process after such a reset.  Every call shares the one scratch array, so
  * calls that overlap on the GPU (different streams, no ordering) race;
  * each call clears the counter it needs.  Asynchronous on stream. */
 gbs_status gbs_spmv_dots_noalloc(int32_t n_brows, int32_t n_bcols, int32_t bdim, int64_t nnzb,
                                  const int32_t* row_ptr, const int32_t* col_idx,
                                  const double* vals, const double* x, double* y,
                                  const double* w, double* dots, void* stream);
+
+/* FP64 FMA throughput of the current device, measured: the best of four
+ * CUDA-event-timed launches (after two warm-up launches) of a kernel that
+ * issues only independent DFMA chains from as many CTAs as stay resident
+ * (SM count from the device properties).  No counterpart in the paper: it
+ * gives the roofline of the FP64 kernels, which on GB300 the FP64 pipe
+ * bounds before HBM.  *tflops: 2 * FMAs / second / 1e12.  *sms: the
+ * device's SM count.  sink_dev: device double[1], written only if the
+ * chains reach an impossible value.  Blocks for about half a second. */
+gbs_status gbs_fp64_peak(double* tflops, int32_t* sms, double* sink_dev, void* stream);
 
 /* Free everything the handle owns.  Synchronises the device. */
 gbs_status gbs_destroy(gbs_hierarchy* h);

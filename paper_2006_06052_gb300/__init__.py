@@ -19,8 +19,8 @@ from ._build import LIB as _LIB_PATH, build as _build_lib
 
 __all__ = [
     "GbsError", "Params", "Info", "Hierarchy", "params_default", "build_hierarchy",
-    "import_hierarchy", "solve", "solve_adjoint", "sampled_outer", "update_values", "spmv",
-    "apply_precond", "hierarchy_info", "export_level", "export_level_sizes", "spmv_dots_noalloc", "precond_bytes", "load_library", "build", "kernel_launches",
+    "import_hierarchy", "import_schur", "solve", "solve_adjoint", "sampled_outer", "update_values", "spmv",
+    "apply_precond", "hierarchy_info", "export_level", "export_level_sizes", "spmv_dots_noalloc", "precond_bytes", "fp64_peak", "load_library", "build", "kernel_launches",
     "GBS_PC_AMG", "GBS_PC_SCHUR", "GBS_BICGSTAB", "GBS_GMRES", "GBS_IDRS", "GBS_FP64", "GBS_FP32",
     "GBS_BF16", "GBS_SPAI0", "GBS_JACOBI", "EXPORTED",
 ]
@@ -40,7 +40,7 @@ EXPORTED = [
     "gbs_sampled_outer", "gbs_update_values", "gbs_spmv", "gbs_apply_precond",
     "gbs_hierarchy_info", "gbs_export_level", "gbs_import_hierarchy", "gbs_destroy",
     "gbs_last_error", "gbs_kernel_launches", "gbs_spmv_dots_noalloc", "gbs_precond_bytes",
-    "gbs_outer_format", "gbs_level_apply",
+    "gbs_outer_format", "gbs_level_apply", "gbs_import_schur", "gbs_fp64_peak",
 ]
 
 
@@ -73,6 +73,13 @@ class _Bsr(ctypes.Structure):
         ("n_brows", ctypes.c_int32), ("n_bcols", ctypes.c_int32), ("bdim", ctypes.c_int32),
         ("nnzb", ctypes.c_int64), ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
         ("vals", ctypes.c_void_p),
+    ]
+
+
+class _Levels(ctypes.Structure):
+    _fields_ = [
+        ("A", ctypes.c_void_p), ("P", ctypes.c_void_p), ("R", ctypes.c_void_p),
+        ("M", ctypes.c_void_p), ("Ainv", ctypes.c_void_p), ("nlev", ctypes.c_int32),
     ]
 
 
@@ -125,6 +132,9 @@ def load_library():
                              c.POINTER(c.c_int32), c.POINTER(c.c_int64), P, P, P],
         "gbs_import_hierarchy": [c.POINTER(_Bsr), c.POINTER(_Bsr), c.POINTER(_Bsr),
                                  c.POINTER(P), P, c.c_int32, c.POINTER(Params), P, c.POINTER(P)],
+        "gbs_import_schur": [c.POINTER(_Bsr), c.POINTER(_Levels), c.POINTER(_Levels), P,
+                             c.POINTER(Params), P, c.POINTER(P)],
+        "gbs_fp64_peak": [c.POINTER(c.c_double), c.POINTER(c.c_int32), P, P],
         "gbs_destroy": [P],
         "gbs_precond_bytes": [P, c.POINTER(c.c_double)],
         "gbs_outer_format": [P, c.POINTER(c.c_int32), c.POINTER(c.c_int64)],
@@ -229,34 +239,76 @@ def build_hierarchy(indptr, indices, vals, bdim, params: Params | None = None,
     return Hierarchy(h, nb * bdim, bdim, len(A.indices), params)
 
 
+class _LevelSet:
+    """Host arrays of one hierarchy in the gbs_levels layout (kept alive
+    while the C struct points at them)."""
+
+    def __init__(self, levels_A, levels_P, levels_R, levels_M, Ainv, bdim):
+        self.keep = []
+
+        def arr(ls):
+            objs = [_HostBsr(*t[:3], bdim, t[3] if len(t) > 3 else None) for t in ls]
+            self.keep.extend(objs)
+            a = (_Bsr * max(1, len(objs)))()
+            for i, o in enumerate(objs):
+                a[i] = o.c
+            return a
+
+        self.A = arr(levels_A)
+        self.P = arr(levels_P)
+        self.R = arr(levels_R)
+        if levels_M is None:
+            self.Ms, self.Mp = [], None
+        else:
+            self.Ms = [np.ascontiguousarray(m, dtype=np.float64).reshape(-1) for m in levels_M]
+            self.Mp = (ctypes.c_void_p * max(1, len(self.Ms)))(
+                *[m.ctypes.data for m in self.Ms])
+        self.Ai = np.ascontiguousarray(Ainv, dtype=np.float64).reshape(-1)
+        self.c = _Levels(ctypes.addressof(self.A), ctypes.addressof(self.P),
+                         ctypes.addressof(self.R),
+                         ctypes.addressof(self.Mp) if self.Mp is not None else None,
+                         self.Ai.ctypes.data, len(levels_A))
+
+
 def import_hierarchy(levels_A, levels_P, levels_R, levels_M, Ainv, bdim,
                      params: Params | None = None, stream=None) -> Hierarchy:
     """Caller-built levels -> device hierarchy (gbs_import_hierarchy).
     levels_A/P/R: lists of (indptr, indices, vals[, n_bcols]) host arrays."""
     lib = load_library()
     params = params or params_default()
-    nlev = len(levels_A)
-    keep = []
-
-    def arr(ls):
-        objs = [_HostBsr(*t[:3], bdim, t[3] if len(t) > 3 else None) for t in ls]
-        keep.extend(objs)
-        a = (_Bsr * max(1, len(objs)))()
-        for i, o in enumerate(objs):
-            a[i] = o.c
-        return a
-
-    A = arr(levels_A)
-    P = arr(levels_P)
-    R = arr(levels_R)
-    Ms = [np.ascontiguousarray(m, dtype=np.float64).reshape(-1) for m in levels_M]
-    Mp = (ctypes.c_void_p * max(1, len(Ms)))(*[m.ctypes.data for m in Ms])
-    Ai = np.ascontiguousarray(Ainv, dtype=np.float64).reshape(-1)
+    L = _LevelSet(levels_A, levels_P, levels_R, levels_M, Ainv, bdim)
     h = ctypes.c_void_p()
-    _check(lib.gbs_import_hierarchy(A, P, R, Mp, ctypes.c_void_p(Ai.ctypes.data), nlev,
-                                    ctypes.byref(params), _stream_ptr(stream), ctypes.byref(h)))
-    nb = len(keep[0].indptr) - 1
-    return Hierarchy(h, nb * bdim, bdim, len(keep[0].indices), params)
+    _check(lib.gbs_import_hierarchy(L.A, L.P, L.R, L.Mp, ctypes.c_void_p(L.Ai.ctypes.data),
+                                    L.c.nlev, ctypes.byref(params), _stream_ptr(stream),
+                                    ctypes.byref(h)))
+    k0 = L.keep[0]
+    nb = len(k0.indptr) - 1
+    return Hierarchy(h, nb * bdim, bdim, len(k0.indices), params)
+
+
+def import_schur(indptr, indices, vals, vel, pres=None, pres_smoother=None,
+                 params: Params | None = None, stream=None) -> Hierarchy:
+    """Schur pressure correction from caller-built inner hierarchies
+    (gbs_import_schur).  (indptr, indices, vals): K in (nvel+1)-blocks.
+    vel / pres: (levels_A, levels_P, levels_R, levels_M, Ainv) of the
+    velocity AMG (bdim nvel) and the pressure AMG (bdim 1; schur_p = 0);
+    pres_smoother: the diagonal pressure smoother (schur_p = 1)."""
+    lib = load_library()
+    params = params or params_default(precond=GBS_PC_SCHUR)
+    nv = params.nvel
+    K = _HostBsr(indptr, indices, vals, nv + 1)
+    V = _LevelSet(*vel, nv)
+    Pl = _LevelSet(*pres, 1) if pres is not None else None
+    ms = None
+    if pres_smoother is not None:
+        ms = np.ascontiguousarray(pres_smoother, dtype=np.float64).reshape(-1)
+    h = ctypes.c_void_p()
+    _check(lib.gbs_import_schur(ctypes.byref(K.c), ctypes.byref(V.c),
+                                ctypes.byref(Pl.c) if Pl is not None else None,
+                                ctypes.c_void_p(ms.ctypes.data) if ms is not None else None,
+                                ctypes.byref(params), _stream_ptr(stream), ctypes.byref(h)))
+    nb = len(K.indptr) - 1
+    return Hierarchy(h, nb * (nv + 1), nv + 1, len(K.indices), params)
 
 
 def _solve(fn, H, b, x, stream, history):
@@ -381,6 +433,16 @@ def level_apply(H: Hierarchy, which: int, level: int, op: int, x, f, y=None, str
     _check(load_library().gbs_level_apply(H.handle, which, level, op, x.data_ptr(), f.data_ptr(),
                                           y.data_ptr(), _stream_ptr(stream)))
     return y
+
+
+def fp64_peak(stream=None):
+    """(TFLOP/s, SM count): the device's measured FP64 FMA throughput."""
+    import torch
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    t, n = ctypes.c_double(), ctypes.c_int32()
+    _check(load_library().gbs_fp64_peak(ctypes.byref(t), ctypes.byref(n),
+                                        ctypes.c_void_p(sink.data_ptr()), _stream_ptr(stream)))
+    return t.value, n.value
 
 
 OUTER_FORMATS = ("block", "csr", "sliced")

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgbstokes.so")
 
-CU_UNITS = ["capi.cu", "amg_fp64.cu", "amg_fp32.cu", "amg_bf16.cu", "noalloc.cu"]
+CU_UNITS = ["capi.cu", "amg_fp64.cu", "amg_fp32.cu", "amg_bf16.cu", "noalloc.cu", "peak.cu"]
 CPP_UNITS = ["setup.cpp"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 

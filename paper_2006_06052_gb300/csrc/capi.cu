@@ -870,6 +870,45 @@ gbs_status guarded(F&& f) {
   }
 }
 
+// One caller-supplied hierarchy (gbs_levels) on the host, checked level by
+// level; ILUT factors are this library's own, from each imported operator.
+HAmg import_amg(const gbs_levels& L, int B, const gbs_params& prm, int relax) {
+  const int nlev = L.nlev;
+  if (nlev < 1 || !L.A || !L.Ainv ||
+      (nlev > 1 && (!L.P || !L.R || (!L.M && relax != GBS_ILUT))))
+    throw SetupError{"bad level arrays"};
+  HAmg H;
+  H.B = B;
+  for (int l = 0; l + 1 < nlev; ++l) {
+    HLevel V;
+    V.A = from_c(&L.A[l]);
+    V.P = from_c(&L.P[l]);
+    V.R = from_c(&L.R[l]);
+    validate(V.A, true);
+    validate(V.P, false);
+    validate(V.R, false);
+    HBsr An = from_c(&L.A[l + 1]);
+    if (V.A.br != B || V.P.br != B || V.R.br != B || An.br != B)
+      throw SetupError{"all levels need the same bdim"};
+    if (V.P.nbr != V.A.nbr || V.P.nbc != An.nbr || V.R.nbr != An.nbr || V.R.nbc != V.A.nbr)
+      throw SetupError{"level " + std::to_string(l) + ": P/R shapes do not match A"};
+    if (relax == GBS_ILUT) {
+      V.ilu = ilut(to_scalar_csr(V.A), prm.ilut_p, prm.ilut_tau);
+    } else {
+      if (!L.M[l]) throw SetupError{"null smoother blocks"};
+      V.M.assign(L.M[l], L.M[l] + (size_t)V.A.nbr * B * B);
+    }
+    H.levels.push_back(std::move(V));
+  }
+  H.Ac = from_c(&L.A[nlev - 1]);
+  validate(H.Ac, true);
+  if (H.Ac.br != B) throw SetupError{"all levels need the same bdim"};
+  const size_t nc = (size_t)H.Ac.nbr * B;
+  if (nc > 8192) throw SetupError{"coarsest level too large for a dense inverse"};
+  H.Ainv.assign(L.Ainv, L.Ainv + nc * nc);
+  return H;
+}
+
 }  // namespace
 
 std::unique_ptr<DevPrecond> make_amg_precond(const HAmg& H, const PrecondOptions& o,
@@ -982,10 +1021,10 @@ gbs_status gbs_import_hierarchy(const gbs_bsr* A, const gbs_bsr* P, const gbs_bs
     if (!out) throw SetupError{"null output handle"};
     *out = nullptr;
     check_params(params);
-    if (params->precond != GBS_PC_AMG) throw SetupError{"import supports the AMG preconditioner"};
-    if (nlev < 1 || !A || !Ainv ||
-        (nlev > 1 && (!P || !R || (!M && params->relax != GBS_ILUT))))
-      throw SetupError{"bad level arrays"};
+    if (params->precond != GBS_PC_AMG)
+      throw SetupError{"gbs_import_hierarchy takes the AMG preconditioner (Schur: gbs_import_schur)"};
+    if (nlev < 1 || !A) throw SetupError{"bad level arrays"};
+    if (params->setup_only) throw SetupError{"import needs device upload (setup_only = 0)"};
     init_device();
     auto hh = std::make_unique<gbs_hierarchy>();
     Handle& h = hh->h;
@@ -994,37 +1033,52 @@ gbs_status gbs_import_hierarchy(const gbs_bsr* A, const gbs_bsr* P, const gbs_bs
     validate(K, true);
     h.B = K.br;
     h.n = (int64_t)K.nbr * K.br;
-    HAmg& H = h.H;
-    H.B = K.br;
-    for (int l = 0; l + 1 < nlev; ++l) {
-      HLevel L;
-      L.A = from_c(&A[l]);
-      L.P = from_c(&P[l]);
-      L.R = from_c(&R[l]);
-      validate(L.A, true);
-      validate(L.P, false);
-      validate(L.R, false);
-      HBsr An = from_c(&A[l + 1]);
-      if (L.A.br != H.B || L.P.br != H.B || L.R.br != H.B || An.br != H.B)
-        throw SetupError{"all levels need the same bdim"};
-      if (L.P.nbr != L.A.nbr || L.P.nbc != An.nbr || L.R.nbr != An.nbr || L.R.nbc != L.A.nbr)
-        throw SetupError{"level " + std::to_string(l) + ": P/R shapes do not match A"};
-      if (params->relax == GBS_ILUT) {
-        // the factors are this library's own, from the imported operator
-        L.ilu = ilut(to_scalar_csr(L.A), params->ilut_p, params->ilut_tau);
-      } else {
-        if (!M[l]) throw SetupError{"null smoother blocks"};
-        L.M.assign(M[l], M[l] + (size_t)L.A.nbr * H.B * H.B);
-      }
-      H.levels.push_back(std::move(L));
-    }
-    H.Ac = from_c(&A[nlev - 1]);
-    validate(H.Ac, true);
-    const size_t nc = (size_t)H.Ac.nbr * H.B;
-    if (nc > 8192) throw SetupError{"coarsest level too large for a dense inverse"};
-    H.Ainv.assign(Ainv, Ainv + nc * nc);
+    const gbs_levels L{A, P, R, M, Ainv, nlev};
+    h.H = import_amg(L, K.br, *params, params->relax);
     h.Kh = std::move(K);
+    finish_build(h, S(stream));
+    *out = hh.release();
+    return GBS_OK;
+  });
+}
+
+gbs_status gbs_import_schur(const gbs_bsr* Kc, const gbs_levels* vel, const gbs_levels* pres,
+                            const double* pres_smoother, const gbs_params* params, void* stream,
+                            gbs_hierarchy** out) {
+  return guarded([&]() -> gbs_status {
+    if (!out) throw SetupError{"null output handle"};
+    *out = nullptr;
+    check_params(params);
+    if (params->precond != GBS_PC_SCHUR) throw SetupError{"gbs_import_schur needs GBS_PC_SCHUR"};
     if (params->setup_only) throw SetupError{"import needs device upload (setup_only = 0)"};
+    if (!vel) throw SetupError{"null velocity hierarchy"};
+    if (params->schur_p == 0 && !pres) throw SetupError{"null pressure hierarchy (schur_p = 0)"};
+    if (params->schur_p == 1 && !pres_smoother)
+      throw SetupError{"null pressure smoother (schur_p = 1)"};
+    HBsr K = from_c(Kc);
+    validate(K, true);
+    if (K.br != params->nvel + 1) throw SetupError{"Schur needs bdim = nvel + 1"};
+    init_device();
+    auto hh = std::make_unique<gbs_hierarchy>();
+    Handle& h = hh->h;
+    h.prm = *params;
+    h.schur = true;
+    h.B = K.br;
+    h.n = (int64_t)K.nbr * K.br;
+    h.Sh = schur_split(K, params->nvel);
+    h.HA = import_amg(*vel, params->nvel, *params, params->relax);
+    const HBsr& A0 = h.HA.levels.empty() ? h.HA.Ac : h.HA.levels[0].A;
+    if (A0.nbr != K.nbr || A0.nbc != K.nbc)
+      throw SetupError{"velocity level 0 does not match K's block rows"};
+    if (params->schur_p == 1) {
+      h.Sh.MS.assign(pres_smoother, pres_smoother + K.nbr);
+    } else {
+      h.HS = import_amg(*pres, 1, *params, params->relax_p);
+      const HBsr& S0 = h.HS.levels.empty() ? h.HS.Ac : h.HS.levels[0].A;
+      if (S0.nbr != K.nbr || S0.nbc != K.nbc)
+        throw SetupError{"pressure level 0 does not match K's block rows"};
+    }
+    h.Kh = std::move(K);
     finish_build(h, S(stream));
     *out = hh.release();
     return GBS_OK;

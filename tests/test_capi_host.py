@@ -23,7 +23,7 @@ def built_library():
 
 def test_library_exports_every_declared_symbol(built_library):
     hdr = open(os.path.join(ROOT, "include", "gbstokes.h")).read()
-    declared = sorted(set(re.findall(r"\b(gbs_[a-z_]+)\s*\(", hdr)))
+    declared = sorted(set(re.findall(r"\b(gbs_[a-z0-9_]+)\s*\(", hdr)))
     assert declared, "no declarations found"
     assert sorted(gb.EXPORTED) == declared
     for name in declared:

@@ -15,6 +15,7 @@ import pytest
 
 import stokes_inputs as si
 from oracle import adjoint, amg, bsr, krylov, schur
+from oracle.precision import round_to
 
 pytestmark = pytest.mark.gpu
 
@@ -214,20 +215,117 @@ def test_mixed_csr_levels_match_block_levels(precision, S, fmt, monkeypatch):
     assert rel_inf(zc, zb) <= 1e-5
 
 
+def _levels(Ho):
+    lv = Ho.levels
+    As = [(L.A.indptr, L.A.indices, L.A.data) for L in lv] + \
+         [(Ho.A_coarse.indptr, Ho.A_coarse.indices, Ho.A_coarse.data)]
+    Ps = [(L.P.indptr, L.P.indices, L.P.data, L.P.n_bcols) for L in lv]
+    Rs = [(L.R.indptr, L.R.indices, L.R.data, L.R.n_bcols) for L in lv]
+    return As, Ps, Rs, [L.M for L in lv], Ho.Ainv_coarse
+
+
+def _import_schur(s, pc, **kw):
+    """The oracle's Schur preconditioner (both inner hierarchies, or the
+    pressure smoother) imported as it is: the GPU runs the same values."""
+    order = 1 if pc.order == "lower" else 0
+    kw.setdefault("krylov", gb.GBS_GMRES)
+    p = gb.params_default(precond=gb.GBS_PC_SCHUR, schur_order=order,
+                          schur_p=0 if pc.HS is not None else 1, **kw)
+    return gb.import_schur(s.indptr, s.indices, s.data, _levels(pc.HA),
+                           _levels(pc.HS) if pc.HS is not None else None,
+                           pc.M_S.reshape(-1) if pc.M_S is not None else None, p)
+
+
+@pytest.mark.parametrize("fmt", ["0", "1", "2", "3"])
+@pytest.mark.parametrize("variant", [("full", "amg"), ("lower", "amg"), ("full", "spai0"),
+                                     ("lower", "jacobi")])
+def test_schur_apply_on_imported_oracle_hierarchy(variant, fmt, monkeypatch):
+    """Eq. SchurPC (Section 4) on the oracle's own velocity and pressure
+    hierarchies: the gather, the coupling kernels (r_p - D u, r_u - G p and
+    their transposes through the transpose map), the inner V-cycles and
+    the scatter match the oracle to 1e-12, forward and transposed, in every
+    level format."""
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
+    order, pressure = variant
+    s = si.make_system("c3", N=9)
+    K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    po = amg.AmgParams(coarse_enough=60)
+    pc = schur.build(K, 3, po, po, order=order, pressure=pressure)
+    H = _import_schur(s, pc)
+    rng = np.random.default_rng(21)
+    for tr in (False, True):
+        r = rng.standard_normal(K.shape[0])
+        z = host(gb.apply_precond(H, dev(r), transpose=tr))
+        ref = pc.apply(r, transpose=tr)
+        assert rel_inf(z, ref) <= 1e-12, (tr, rel_inf(z, ref))
+
+
+def test_schur_import_rejects_mismatched_levels():
+    s = si.make_system("c3", N=6)
+    K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    po = amg.AmgParams(coarse_enough=40)
+    pc = schur.build(K, 3, po, po)
+    s5 = si.make_system("c3", N=5)
+    other = schur.build(bsr.from_arrays(s5.indptr, s5.indices, s5.data, 4), 3, po, po)
+    p = gb.params_default(precond=gb.GBS_PC_SCHUR, krylov=gb.GBS_GMRES)
+    with pytest.raises(gb.GbsError) as e:
+        gb.import_schur(s.indptr, s.indices, s.data, _levels(other.HA), _levels(pc.HS), None, p)
+    assert e.value.status == -1
+    with pytest.raises(gb.GbsError):
+        gb.import_schur(s.indptr, s.indices, s.data, _levels(pc.HA), None, None, p)
+
+
+FMT = {gb.GBS_FP32: "fp32", gb.GBS_BF16: "bf16"}
+
+
+@pytest.mark.parametrize("fmt", ["0", "1", "2", "3"])
 @pytest.mark.parametrize("precision", [gb.GBS_FP32, gb.GBS_BF16])
-def test_mixed_vcycle_close_to_fp64(precision):
-    """Mixed forms: the cast hierarchy's V-cycle stays within the storage
-    precision of the FP64 one (FP32 ~1e-6, BF16 ~1e-2 relative)."""
+def test_mixed_vcycle_matches_oracle_on_cast_hierarchy(precision, fmt, monkeypatch):
+    """Mixed forms (Section 4, Listing V4; BF16 storage with FP32
+    accumulation) against the oracle's FP64 V-cycle run on the same
+    hierarchy with every stored value rounded exactly as the library
+    uploads it (oracle.amg.cast_values) and the input rounded to FP32, as
+    it enters the V-cycle.  What remains is FP32 accumulation and FP32
+    vector storage: a few units of 2^-24 per operation over the levels, so
+    1e-5 relative in the max norm for both forms.  Formats 2 and 3 put
+    every level in scalar CSR and in slices (the staged bulk-copy
+    kernels)."""
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
     s = si.make_system("c2", N=10)
-    p64 = gb.params_default(relax=gb.GBS_JACOBI, coarse_enough=60)
-    pmx = gb.params_default(relax=gb.GBS_JACOBI, coarse_enough=60, precision=precision)
-    H64 = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, p64)
-    Hmx = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, pmx)
-    r = dev(np.random.default_rng(2).standard_normal(s.n))
-    z64 = host(gb.apply_precond(H64, r))
-    zmx = host(gb.apply_precond(Hmx, r))
-    tol = 1e-4 if precision == gb.GBS_FP32 else 1e-1
-    assert rel_inf(zmx, z64) <= tol
+    A = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    Ho = amg.build_hierarchy(A, amg.AmgParams(coarse_enough=60, relax="jacobi"))
+    H = _import(Ho, 4, relax=gb.GBS_JACOBI, precision=precision)
+    Hc = amg.cast_values(Ho, FMT[precision])
+    rng = np.random.default_rng(31)
+    for tr in (False, True):
+        r = rng.standard_normal(A.shape[0])
+        z = host(gb.apply_precond(H, dev(r), transpose=tr))
+        ref = amg.vcycle(Hc, round_to(r, "fp32"), 0, transpose=tr)
+        assert rel_inf(z, ref) <= 1e-5, (tr, rel_inf(z, ref))
+        if precision == gb.GBS_BF16:
+            # BF16 storage rounding, not the accumulation, separates it from FP64
+            z64 = amg.vcycle(Ho, r, 0, transpose=tr)
+            assert rel_inf(z, z64) > 10 * rel_inf(z, ref)
+
+
+@pytest.mark.parametrize("fmt", ["0", "3"])
+@pytest.mark.parametrize("precision", [gb.GBS_FP32, gb.GBS_BF16])
+def test_mixed_schur_matches_oracle_on_cast_hierarchy(precision, fmt, monkeypatch):
+    """The Schur preconditioner in the mixed forms against the oracle on
+    the cast values (velocity and pressure hierarchies, G and D), 1e-5."""
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
+    s = si.make_system("c3", N=10)
+    K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    po = amg.AmgParams(coarse_enough=60)
+    pc = schur.build(K, 3, po, po)
+    H = _import_schur(s, pc, precision=precision)
+    pcc = schur.cast_values(pc, FMT[precision])
+    rng = np.random.default_rng(41)
+    for tr in (False, True):
+        r = rng.standard_normal(K.shape[0])
+        z = host(gb.apply_precond(H, dev(r), transpose=tr))
+        ref = pcc.apply(round_to(r, "fp32"), transpose=tr)
+        assert rel_inf(z, ref) <= 1e-5, (tr, rel_inf(z, ref))
 
 
 # ----------------------------------------------------------------- solves
@@ -421,17 +519,80 @@ def test_full_size_c2_against_oracle():
     assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-5
 
 
-@pytest.mark.parametrize("precision", [gb.GBS_FP64, gb.GBS_BF16])
-def test_full_size_c3_true_residual(precision):
-    """C3 at full size (N=128, 8,388,608 unknowns): the FP64 true residual,
-    recomputed on the host with the oracle's SpMV, is <= 1e-8."""
-    s = si.make_system("c3")
-    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4, _params(s, precision=precision,
-                                                                    enable_adjoint=0))
+def _exported(H, which):
+    """Every level of hierarchy `which` of a handle, as gbs_export_level
+    returns it (the FP64 setup values), in import_hierarchy's layout."""
+    nl = gb.hierarchy_info(H, which)["nlevels"]
+    As, Ps, Rs, Ms = [], [], [], []
+    for l in range(nl):
+        As.append(gb.export_level(H, which, l, 0))
+        if l + 1 < nl:
+            Ps.append(gb.export_level(H, which, l, 1))
+            Rs.append(gb.export_level(H, which, l, 2))
+            Ms.append(gb.export_level(H, which, l, 3))
+    return As, Ps, Rs, Ms, gb.export_level(H, which, nl - 1, 5)
+
+
+_C3 = {}
+
+
+def _c3_handle(precision):
+    """The full-size N=128 Schur system; the host setup runs once (FP64
+    handle) and the mixed forms import its exported hierarchies."""
+    if "fp64" not in _C3:
+        s = si.make_system("c3")
+        _C3["s"] = s
+        _C3["fp64"] = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
+                                         _params(s, enable_adjoint=0))
+    s, H64 = _C3["s"], _C3["fp64"]
+    if precision == gb.GBS_FP64:
+        return s, H64
+    return s, gb.import_schur(s.indptr, s.indices, s.data, _exported(H64, 0), _exported(H64, 1),
+                              None, _params(s, precision=precision, enable_adjoint=0))
+
+
+def c3_error_vs_oracle(x, g, n):
+    """||x - x_oracle|| / ||x_oracle|| estimated from the oracle solution's
+    stored sample (uniform indices): sqrt(n/m sum (x_i - xo_i)^2) / ||xo||."""
+    idx = np.array(g["sample_idx"], dtype=np.int64)
+    xs = np.array(g["sample_x"])
+    return float(np.sqrt(n / len(idx) * np.sum((x[idx] - xs) ** 2)) / g["x_norm"][0])
+
+
+@pytest.mark.parametrize("precision", [gb.GBS_FP64, gb.GBS_FP32, gb.GBS_BF16])
+def test_full_size_c3_against_oracle(precision):
+    """C3 at full size (N=128, 8,388,608 unknowns, Schur + GMRES(30)) in
+    each hierarchy form, against the oracle's own full-size solve
+    (tests/golden/c3_oracle_solution.txt, written by make_c3_oracle.py):
+    the FP64 true residual recomputed on the host is <= 1e-8; the FP64
+    form's iteration count is within +-10% of the oracle's; every form's
+    error against the oracle solution is reported and bounded."""
+    from conftest import load_golden
+    g = load_golden("c3_oracle_solution.txt")
+    s, H = _c3_handle(precision)
+    assert int(g["n"][0]) == s.n
     x, info = gb.solve(H, dev(s.b))
     x = host(x)
-    assert info.converged
-    assert _true_rel(s, x) <= 1e-8
+    rel = _true_rel(s, x)
+    io = int(g["iterations"][0])
+    err = c3_error_vs_oracle(x, g, s.n)
+    norm_dev = abs(np.linalg.norm(x) - g["x_norm"][0]) / g["x_norm"][0]
+    print("C3 form %d: iterations %d (oracle %d), true rel. residual %.3e, "
+          "||x - x_oracle||/||x_oracle|| ~ %.3e, | ||x|| - ||x_oracle|| |/||x_oracle|| %.3e"
+          % (precision, info.iters, io, rel, err, norm_dev))
+    assert info.converged and rel <= 1e-8
+    if precision == gb.GBS_FP64:
+        assert abs(info.iters - io) <= max(1, math.ceil(0.1 * io)), (info.iters, io)
+    bound = C3_ERR_BOUND[precision]
+    assert err <= bound and norm_dev <= bound, (err, norm_dev)
+
+
+# Two solutions that both meet ||b - K x|| <= 1e-8 ||b|| may differ by up to
+# cond(K) * 2e-8 relative.  The FP64 form takes the oracle's own path (same
+# hierarchy, same Krylov steps: measured 1.7e-15), so it is held to 1e-10;
+# the mixed forms stop at a different iterate (measured 3.8e-8 FP32,
+# 1.3e-7 BF16) and are held to 1e-5, the bound of the C3 small-grid test.
+C3_ERR_BOUND = {gb.GBS_FP64: 1e-10, gb.GBS_FP32: 1e-5, gb.GBS_BF16: 1e-5}
 
 
 def test_full_size_c4_adjoint_central_differences():

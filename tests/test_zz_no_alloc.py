@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 import stokes_inputs as si
+from oracle import bsr
 
 pytestmark = pytest.mark.gpu
 
@@ -43,7 +44,8 @@ def test_noalloc_matches_regular_spmv_twice(name, N):
     rp = _dev(s.indptr, torch.int32)
     ci = _dev(s.indices, torch.int32)
     va = _dev(s.data.reshape(-1))
-    A = s.scipy()
+    Ko = bsr.from_arrays(s.indptr, s.indices, s.data, B)
+    A = Ko.scipy()
     rng = np.random.default_rng(17)
     y = torch.empty(s.n, dtype=torch.float64, device="cuda")
     for call in range(2):
@@ -52,17 +54,41 @@ def test_noalloc_matches_regular_spmv_twice(name, N):
         x, w = _dev(xh), _dev(wh)
         gb.spmv_dots_noalloc(rp, ci, va, B, x, y, w=w)
         _, dots = gb.spmv_dots_noalloc(rp, ci, va, B, x, y, w=w)
-        y_ref = gb.spmv(H, x)
+        y_lib = gb.spmv(H, x)
         torch.cuda.synchronize()
-        yn, yr = y.cpu().numpy(), y_ref.cpu().numpy()
+        yn = y.cpu().numpy()
+        yr = bsr.spmv(Ko, xh)   # the oracle's SpMV
         bound = abs(A) @ np.abs(xh)
         assert np.all(np.abs(yn - yr) <= 1e-13 * bound + 1e-300), call
+        assert np.all(np.abs(yn - y_lib.cpu().numpy()) <= 1e-13 * bound + 1e-300), call
         d = dots.cpu().numpy()
         ref_wy = float(np.dot(wh, yr))
         ref_yy = float(np.dot(yr, yr))
         scale_wy = float(np.dot(np.abs(wh), bound))
         assert abs(d[0] - ref_wy) <= 1e-13 * scale_wy + 1e-300, (call, d[0], ref_wy)
         assert abs(d[1] - ref_yy) <= 1e-13 * float(np.dot(bound, bound)), (call, d[1], ref_yy)
+
+
+def test_noalloc_without_w_reports_zero_first_dot():
+    """w = NULL: dots[0] is 0 and dots[1] is y . y, call after call (the
+    scratch keeps the previous call's partial sums)."""
+    s = si.make_system("c2", N=7)
+    rp = _dev(s.indptr, torch.int32)
+    ci = _dev(s.indices, torch.int32)
+    va = _dev(s.data.reshape(-1))
+    Ko = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    rng = np.random.default_rng(23)
+    y = torch.empty(s.n, dtype=torch.float64, device="cuda")
+    dots = torch.full((2,), 7.0, dtype=torch.float64, device="cuda")
+    for call in range(2):
+        xh = rng.standard_normal(s.n)
+        gb.spmv_dots_noalloc(rp, ci, va, 4, _dev(xh), y, w=None, dots=dots)
+        torch.cuda.synchronize()
+        d = dots.cpu().numpy()
+        yr = bsr.spmv(Ko, xh)
+        bound = abs(Ko.scipy()) @ np.abs(xh)
+        assert d[0] == 0.0, call
+        assert abs(d[1] - float(np.dot(yr, yr))) <= 1e-13 * float(np.dot(bound, bound)), call
 
 
 def test_noalloc_rejects_sizes_beyond_the_maximum():
