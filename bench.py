@@ -281,6 +281,7 @@ def mixed_forms(gb, si, args, s_main, H_main, spec_main):
     (sampled estimate) and against this run's FP64 solution."""
     import torch
     out = {}
+    kw = {} if args.gmres_reorth is None else {"gmres_reorth": args.gmres_reorth}
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     sampler.start()
     for name in ("c2", "c3"):
@@ -291,7 +292,7 @@ def mixed_forms(gb, si, args, s_main, H_main, spec_main):
             s = si.make_system(name)
             t0 = time.perf_counter()
             H64 = gb.build_hierarchy(s.indptr, s.indices, s.data, s.bdim,
-                                     solver_params(gb, wl, use_graph=1))
+                                     solver_params(gb, wl, use_graph=1, **kw))
             torch.cuda.synchronize()
             setup_s = time.perf_counter() - t0
         b = torch.as_tensor(s.b, device="cuda")
@@ -301,7 +302,7 @@ def mixed_forms(gb, si, args, s_main, H_main, spec_main):
             if prec == 0:
                 H = H64
             else:
-                p = solver_params(gb, wl, use_graph=1)
+                p = solver_params(gb, wl, use_graph=1, **kw)
                 p.precision = prec
                 if name == "c3":
                     H = gb.import_schur(s.indptr, s.indices, s.data, exported(gb, H64, 0),
@@ -457,6 +458,8 @@ def main():
                     help="c3 workloads: 0 pressure AMG V-cycle, 1 one SPAI0 application on S_hat")
     ap.add_argument("--krylov", default=None, choices=["bicgstab", "gmres", "idrs"],
                     help="outer solver (default: the workload's: BiCGStab for c1/c2, GMRES(30) for c3)")
+    ap.add_argument("--gmres-reorth", type=int, default=None, choices=[0, 1, 2],
+                    help="GMRES second Gram-Schmidt pass: 0 never, 1 DGKS test, 2 always")
     ap.add_argument("--level-format", type=int, default=0,
                     help="0 scalar CSR for mostly-zero block levels, 1 block form everywhere")
     ap.add_argument("--plain-aggregation", action="store_true",
@@ -490,6 +493,8 @@ def main():
                            "idrs": gb.GBS_IDRS}[args.krylov]
     if spec["system"] == "c3":
         extra.update(schur_order=args.schur_order, schur_p=args.schur_p)
+    if args.gmres_reorth is not None:
+        extra["gmres_reorth"] = args.gmres_reorth
     if args.relax:
         extra["relax"] = {"spai0": gb.GBS_SPAI0, "jacobi": gb.GBS_JACOBI,
                           "ilut": gb.GBS_ILUT}[args.relax]

@@ -126,6 +126,17 @@ typedef struct {
   double ilut_tau;        /* drop tolerance (1e-2) */
   int32_t ilut_sweeps;    /* Jacobi sweeps per triangular solve (2; 0..16) */
   double ilut_omega;      /* damping (1) */
+  int32_t gmres_reorth;   /* GMRES orthogonalisation against the basis:
+                             0 classical Gram-Schmidt, one pass (default); 1 a
+                             second pass when ||w|| drops below ||w_before|| /
+                             sqrt(2) (DGKS); 2 always two passes.  Every restart
+                             begins from the true residual, so a less orthogonal
+                             basis costs iterations, never accuracy */
+  int32_t wait_log2;      /* each wait of the FP32/BF16 bulk-copy pipelines gives
+                             up after 2^wait_log2 SM clocks (31: about a second;
+                             0..40); the solve then returns GBS_ERR_CUDA.  Small
+                             values exist to test that path: the copies still
+                             land before the kernel returns */
 } gbs_params;
 
 typedef struct {

@@ -65,6 +65,7 @@ class Params(ctypes.Structure):
         ("idr_s", ctypes.c_int32), ("idr_seed", ctypes.c_int32),
         ("ilut_p", ctypes.c_double), ("ilut_tau", ctypes.c_double),
         ("ilut_sweeps", ctypes.c_int32), ("ilut_omega", ctypes.c_double),
+        ("gmres_reorth", ctypes.c_int32), ("wait_log2", ctypes.c_int32),
     ]
 
 

@@ -119,6 +119,51 @@ DevCsr<VT> upload_csr(Arena& ar, const HCsr& C, cudaStream_t s, std::vector<std:
   return d;
 }
 
+template <class VT>
+DevBSell<VT> upload_bsell(Arena& ar, const HBSell& S, cudaStream_t s,
+                          std::vector<std::vector<VT>>& keep) {
+  DevBSell<VT> d;
+  d.nbr = S.nbr;
+  d.nslices = S.nslices;
+  d.perm = ar.upload(S.perm.data(), S.perm.size(), s);
+  d.off = ar.upload(S.off.data(), S.off.size(), s);
+  d.col = ar.upload(S.col.data(), S.col.size(), s);
+  keep.push_back(cast_vec<VT>(S.val));
+  d.val = ar.upload(keep.back().data(), keep.back().size(), s);
+  return d;
+}
+
+// Block-row slices (HBSell) for a block level of an FP64 form: the FP64
+// pipe bounds those kernels, and the sorted slices give every lane a whole
+// row of nearly the common length, with no cross-lane sums.  Taken when
+// the level has at least 32k scalar rows (a warp per slice then still
+// fills the GPU), runs one lane per scalar row (G = 0), and padding adds
+// at most 15%.  GBS_BSELL=0 / 1 switches the choice off / forces it on
+// every square block level (tests).
+constexpr int BSELL_WINDOW = 32;   // slices per sorting window
+template <class AT>
+inline bool use_bsell(const HBsr& H, int G) {
+  if (H.br != H.bc) return false;
+  if (const char* e = std::getenv("GBS_BSELL")) {
+    if (e[0] == '0') return false;
+    if (e[0] == '1') return true;
+  }
+  if (sizeof(AT) != 8 || G != 0 || (int64_t)H.nbr * H.br < 32768) return false;
+  return bsell_padding(H, BSELL_WINDOW) <= 0.15;
+}
+
+// Zero-guess pre-smoothing fused with the residual (x = M f, r = f - (A M) f)
+// on FP64 levels that run in slices, with one pre-sweep of SPAI0 or Jacobi:
+// one pass instead of two, and no wait for x between them.  The mixed forms
+// keep the two passes (A M rounded to FP32/BF16 is not A and M rounded).
+// GBS_FUSE=0 switches it off (measurement and tests).
+template <class AT>
+inline bool use_fused(const HLevel& h, const PrecondOptions& o) {
+  if (sizeof(AT) != 8 || o.npre != 1 || !h.ilu.d.empty() || h.M.empty()) return false;
+  if (const char* e = std::getenv("GBS_FUSE")) return e[0] != '0';
+  return true;
+}
+
 // Per-level format choice: a level whose stored blocks are at most half
 // nonzero is kept as scalar CSR of its nonzeros (fewer bytes and, on the
 // FP64 pipe, fewer FMAs); dense-block levels stay block CSR.
@@ -136,15 +181,26 @@ inline bool use_scalar_csr(const HBsr& H, int level_format) {
 // Sliced layout of a scalar CSR operator (sell.cuh): automatic when
 // padding each slice to its longest row adds at most 10% entries; format 3
 // forces it wherever B divides the rows, format 2 keeps plain CSR.
-inline bool use_sell(const HCsr& C, int B, int level_format) {
+// 0 plain CSR, 1 slices in natural node order, 2 slices in sorted node
+// order (HSell::node).  An irregular operator pads little once its nodes
+// are sorted by row length, and its lanes then need no cross-lane sums,
+// but the 32 rows of a slice come from 32 places in a window of 1024 nodes
+// and their x gathers no longer share cache lines: measured slower in every
+// form (C3 FP64 129 -> 181 ms, BF16 94 -> 146 ms with the velocity levels
+// and transfer operators sorted).  So sorted slices are used only when
+// GBS_SELL_SORT=1 forces them (tests).
+inline int use_sell(const HCsr& C, int B, int level_format) {
   const int f = level_format_of(level_format);
-  if (B < 1 || C.n == 0 || C.n % B != 0 || f == 2) return false;
-  if (f == 3) return true;
-  return sell_padding(C, B) <= 0.10;   // 0.4 measured slower in every form
+  if (B < 1 || C.n == 0 || C.n % B != 0 || f == 2) return 0;
+  const double pad = sell_padding(C, B);
+  if (const char* e = std::getenv("GBS_SELL_SORT"))
+    if (e[0] == '1' && pad > 0.01) return 2;
+  if (f == 3) return 1;
+  return pad <= 0.10 ? 1 : 0;   // 0.4 measured slower in every form
 }
 
 template <class VT>
-DevSell<VT> upload_sell(Arena& ar, const HSell& S, double* err, cudaStream_t s,
+DevSell<VT> upload_sell(Arena& ar, const HSell& S, double* err, long long wait, cudaStream_t s,
                         std::vector<std::vector<VT>>& keep) {
   DevSell<VT> d;
   d.n = S.n;
@@ -155,7 +211,11 @@ DevSell<VT> upload_sell(Arena& ar, const HSell& S, double* err, cudaStream_t s,
   keep.push_back(cast_vec<VT>(S.val));
   d.val = ar.upload(keep.back().data(), keep.back().size(), s);
   d.err = err;
+  d.wait = wait;
   d.cinfo = ar.upload(S.cinfo.data(), S.cinfo.size(), s);
+  if (!S.node.empty()) d.node = ar.upload(S.node.data(), S.node.size(), s);
+  d.uniform = S.nslices > 0 && std::all_of(S.cinfo.begin(), S.cinfo.end(),
+                                           [](int32_t c) { return c < 0; });
   if (!S.uoff.empty()) {
     std::vector<int2> ui(S.uoff.size());
     for (size_t k = 0; k < ui.size(); ++k) ui[k] = make_int2(S.uoff[k], (int)S.umask[k]);
@@ -166,11 +226,21 @@ DevSell<VT> upload_sell(Arena& ar, const HSell& S, double* err, cudaStream_t s,
 }
 
 // Staged (bulk-copy pipeline) kernels for FP32/BF16 forms, direct loads for
-// FP64 (sell.cuh).
+// FP64 (sell.cuh).  The direct kernels would stream only the values of a
+// uniform (stencil) operator in the mixed forms, 2 or 4 bytes an entry
+// against 6 or 8 with staged column indices, but measured slower there
+// (C2 BF16 solve 13.5 ms direct, 13.1 staged): GBS_SELL_DIRECT=1 sends the
+// mixed forms' uniform operators to them, =0 keeps every one staged.
+template <class VT, class AT>
+inline bool sell_direct(const DevSell<VT>& A) {
+  if (sizeof(AT) == 8) return true;
+  if (const char* e = std::getenv("GBS_SELL_DIRECT")) return e[0] == '1';
+  return false;
+}
 template <int MODE, class VT, class XT, class YT, class AT>
 void sell_spmv(const DevSell<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
   if (A.n == 0) return;
-  if constexpr (sizeof(AT) == 8) {
+  if (sell_direct<VT, AT>(A)) {
     k_sell_spmv_direct<MODE, VT, XT, YT, AT>
         <<<grid_for((int64_t)A.nslices * 32), 256, 0, s>>>(A, x, f, y);
   } else {
@@ -179,26 +249,28 @@ void sell_spmv(const DevSell<VT>& A, const XT* x, const YT* f, YT* y, cudaStream
   }
   GBS_LAUNCH_CHECK();
 }
-template <int B, class VT, class XT, class AT>
-void sell_relax_B(const DevSell<VT>& A, const VT* M, const XT* f, const XT* x, XT* xo,
+template <int B, class VT, class XT, class AT, class OT>
+void sell_relax_B(const DevSell<VT>& A, const VT* M, const XT* f, const XT* x, OT* xo,
                   cudaStream_t s) {
   const int64_t groups = (int64_t)A.nslices / B;
-  if constexpr (sizeof(AT) == 8) {
-    k_sell_relax_direct<B, VT, XT, AT><<<grid_for(groups * 32), 256, 0, s>>>(A, M, f, x, xo);
+  if (sell_direct<VT, AT>(A)) {
+    k_sell_relax_direct<B, VT, XT, AT, OT><<<grid_for(groups * 32), 256, 0, s>>>(A, M, f, x, xo);
   } else {
-    launch_sell(k_sell_relax<B, VT, XT, AT>, sell_smem_bytes<VT>(),
+    launch_sell(k_sell_relax<B, VT, XT, AT, OT>, sell_smem_bytes<VT>(),
                 (groups + SELL_WARPS - 1) / SELL_WARPS, s, A, M, f, x, xo);
   }
 }
-template <class VT, class XT, class AT>
-void sell_relax(int B, const DevSell<VT>& A, const VT* M, const XT* f, const XT* x, XT* xo,
+// xo = x + M (f - A x) on a sliced level; OT: the output's type (the last
+// level-0 sweep of a mixed form writes the FP64 preconditioner output).
+template <class VT, class XT, class AT, class OT = XT>
+void sell_relax(int B, const DevSell<VT>& A, const VT* M, const XT* f, const XT* x, OT* xo,
                 cudaStream_t s) {
   if (A.n == 0) return;
   switch (B) {
-    case 1: sell_relax_B<1, VT, XT, AT>(A, M, f, x, xo, s); break;
-    case 2: sell_relax_B<2, VT, XT, AT>(A, M, f, x, xo, s); break;
-    case 3: sell_relax_B<3, VT, XT, AT>(A, M, f, x, xo, s); break;
-    case 4: sell_relax_B<4, VT, XT, AT>(A, M, f, x, xo, s); break;
+    case 1: sell_relax_B<1, VT, XT, AT, OT>(A, M, f, x, xo, s); break;
+    case 2: sell_relax_B<2, VT, XT, AT, OT>(A, M, f, x, xo, s); break;
+    case 3: sell_relax_B<3, VT, XT, AT, OT>(A, M, f, x, xo, s); break;
+    case 4: sell_relax_B<4, VT, XT, AT, OT>(A, M, f, x, xo, s); break;
   }
   GBS_LAUNCH_CHECK();
 }
@@ -237,6 +309,32 @@ void csr_relax(int B, DevCsr<VT> A, const VT* M, const XT* f, const XT* x, XT* x
     case 2: csr_relax_B<2, VT, XT, AT>(A, M, f, x, xo, s); break;
     case 3: csr_relax_B<3, VT, XT, AT>(A, M, f, x, xo, s); break;
     case 4: csr_relax_B<4, VT, XT, AT>(A, M, f, x, xo, s); break;
+  }
+  GBS_LAUNCH_CHECK();
+}
+
+template <int MODE, class VT, class XT, class YT, class AT>
+void bsell_spmv(int B, const DevBSell<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
+  if (A.nslices == 0) return;
+  const unsigned g = grid_for((int64_t)A.nslices * 32);
+  switch (B) {
+    case 1: k_bsell_spmv<1, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(A, x, f, y); break;
+    case 2: k_bsell_spmv<2, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(A, x, f, y); break;
+    case 3: k_bsell_spmv<3, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(A, x, f, y); break;
+    case 4: k_bsell_spmv<4, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(A, x, f, y); break;
+  }
+  GBS_LAUNCH_CHECK();
+}
+template <class VT, class XT, class AT>
+void bsell_relax(int B, const DevBSell<VT>& A, const VT* M, const XT* f, const XT* x, XT* xo,
+                 cudaStream_t s) {
+  if (A.nslices == 0) return;
+  const unsigned g = grid_for((int64_t)A.nslices * 32);
+  switch (B) {
+    case 1: k_bsell_relax<1, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, xo); break;
+    case 2: k_bsell_relax<2, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, xo); break;
+    case 3: k_bsell_relax<3, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, xo); break;
+    case 4: k_bsell_relax<4, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, xo); break;
   }
   GBS_LAUNCH_CHECK();
 }
@@ -348,6 +446,15 @@ struct DevAmg {
     int64_t nnz_Li = 0, nnz_Ui = 0;
     bool a_csr = false, p_csr = false, r_csr = false;
     bool a_sell = false, p_sell = false, r_sell = false;
+    DevBSell<VT> Ab;                    // block-row slices of A (FP64 block levels)
+    bool a_bsell = false;
+    int64_t slots_Ab = 0;
+    // fused zero-guess pre-smoothing + residual (FP64 forms): A M in the
+    // level's slices (fused 1: scalar slices AMs; 2: block-row slices AMb)
+    int fused = 0;
+    DevSell<VT> AMs;
+    DevBSell<VT> AMb;
+    int64_t slots_AM = 0, sl_AM = 0;
     const VT* M = nullptr;
     ST *f = nullptr, *r = nullptr, *x = nullptr, *xt = nullptr, *e = nullptr;
     int64_t n = 0;
@@ -383,17 +490,25 @@ struct DevAmg {
       // the block form of A stays resident when the adjoint may need A^T
       if (!L.a_csr || o.tmaps) L.A = upload_bsr<VT, AT>(ar, h.A, o.tmaps, s, keep);
       else { L.A.nbr = h.A.nbr; L.A.nbc = h.A.nbc; }
+      if (!L.a_csr && use_bsell<AT>(h.A, L.A.G)) {
+        const HBSell Sb = to_bsell(h.A, BSELL_WINDOW);
+        L.Ab = upload_bsell<VT>(ar, Sb, s, keep);
+        L.a_bsell = true;
+        L.slots_Ab = (int64_t)Sb.col.size();
+        GBS_CUDA(cudaStreamSynchronize(s));  // Sb's host arrays die here
+      }
       // scalar CSR, as plain rows or in slices
       auto scalar = [&](const HBsr& Hm, DevCsr<VT>& dc, DevSell<VT>& ds, bool& sl, int64_t& nnz,
                         int64_t& slots, int64_t& nsl) {
         HCsr c = to_scalar_csr(Hm);
         nnz = (int64_t)c.col.size();
-        sl = use_sell(c, B, o.level_format);
+        const int how = use_sell(c, B, o.level_format);
+        sl = how != 0;
         if (sl) {
-          const HSell S = to_sell(c, B);
+          const HSell S = to_sell(c, B, how == 2);
           slots = (int64_t)S.col.size();
           nsl = S.nslices;
-          ds = upload_sell<VT>(ar, S, o.err, s, keep);
+          ds = upload_sell<VT>(ar, S, o.err, o.wait_cycles, s, keep);
           GBS_CUDA(cudaStreamSynchronize(s));  // S's host arrays die here
         } else {
           dc = upload_csr<VT>(ar, c, s, keep);
@@ -427,6 +542,27 @@ struct DevAmg {
         L.nnz_Li = (int64_t)h.ilu.L.col.size();
         L.nnz_Ui = (int64_t)h.ilu.U.col.size();
         GBS_CUDA(cudaStreamSynchronize(s));  // host staging (Us, transposes) dies here
+      }
+      if (use_fused<AT>(h, o) && (L.a_sell || L.a_bsell)) {
+        const HBsr AM = scale_columns(h.A, h.M);
+        if (L.a_bsell) {
+          const HBSell Sb = to_bsell(AM, BSELL_WINDOW);
+          L.AMb = upload_bsell<VT>(ar, Sb, s, keep);
+          L.slots_AM = (int64_t)Sb.col.size();
+          L.fused = 2;
+          GBS_CUDA(cudaStreamSynchronize(s));
+        } else {
+          const HCsr c = to_scalar_csr(AM);
+          const int how = use_sell(c, B, o.level_format);
+          if (how) {
+            const HSell Sa = to_sell(c, B, how == 2);
+            L.AMs = upload_sell<VT>(ar, Sa, o.err, o.wait_cycles, s, keep);
+            L.slots_AM = (int64_t)Sa.col.size();
+            L.sl_AM = Sa.nslices;
+            L.fused = 1;
+            GBS_CUDA(cudaStreamSynchronize(s));
+          }
+        }
       }
       L.f = ar.alloc<ST>(L.n);
       L.r = ar.alloc<ST>(L.n);
@@ -491,7 +627,8 @@ struct DevAmg {
   template <bool TR>
   void resid(Lev& L, const ST* x, const ST* f, ST* r, cudaStream_t s) {
     const bool acsr = L.a_csr && !TR;   // A^T goes through the block form's transpose map
-    if (acsr && L.a_sell) sell_spmv<SPMV_RESID, VT, ST, ST, AT>(L.As, x, f, r, s);
+    if (L.a_bsell && !TR) bsell_spmv<SPMV_RESID, VT, ST, ST, AT>(B, L.Ab, x, f, r, s);
+    else if (acsr && L.a_sell) sell_spmv<SPMV_RESID, VT, ST, ST, AT>(L.As, x, f, r, s);
     else if (acsr) csr_spmv<SPMV_RESID, VT, ST, ST, AT>(L.Ac, x, f, r, s);
     else spmv<TR, SPMV_RESID, VT, ST, ST, AT>(B, L.A, x, f, r, s);
   }
@@ -505,6 +642,8 @@ struct DevAmg {
       const ST* z = ilu_apply<TR>(L, L.r, s);
       k_vaxpy<ST><<<grid_for(L.n), 256, 0, s>>>(L.n, xin, (ST)ilu_omega, z, xout);
       GBS_LAUNCH_CHECK();
+    } else if (L.a_bsell && !TR) {
+      bsell_relax<VT, ST, AT>(B, L.Ab, L.M, f, xin, xout, s);
     } else if (acsr && L.a_sell) {
       sell_relax<VT, ST, AT>(B, L.As, L.M, f, xin, xout, s);
     } else if (acsr) {
@@ -514,13 +653,50 @@ struct DevAmg {
     }
   }
 
+  // x = M f and r = f - A x (zero-guess pre-smoothing + residual, fused).
+  void presmooth_resid(Lev& L, const ST* f, ST* x, ST* r, cudaStream_t s) {
+    if (L.fused == 2) {
+      const unsigned g = grid_for((int64_t)L.AMb.nslices * 32);
+      switch (B) {
+        case 1: k_bsell_presmooth<1, VT, ST, AT><<<g, 256, 0, s>>>(L.AMb, L.M, f, x, r); break;
+        case 2: k_bsell_presmooth<2, VT, ST, AT><<<g, 256, 0, s>>>(L.AMb, L.M, f, x, r); break;
+        case 3: k_bsell_presmooth<3, VT, ST, AT><<<g, 256, 0, s>>>(L.AMb, L.M, f, x, r); break;
+        case 4: k_bsell_presmooth<4, VT, ST, AT><<<g, 256, 0, s>>>(L.AMb, L.M, f, x, r); break;
+      }
+    } else {
+      const unsigned g = grid_for((int64_t)(L.AMs.nslices / B) * 32);
+      switch (B) {
+        case 1: k_sell_presmooth_direct<1, VT, ST, AT><<<g, 256, 0, s>>>(L.AMs, L.M, f, x, r); break;
+        case 2: k_sell_presmooth_direct<2, VT, ST, AT><<<g, 256, 0, s>>>(L.AMs, L.M, f, x, r); break;
+        case 3: k_sell_presmooth_direct<3, VT, ST, AT><<<g, 256, 0, s>>>(L.AMs, L.M, f, x, r); break;
+        case 4: k_sell_presmooth_direct<4, VT, ST, AT><<<g, 256, 0, s>>>(L.AMs, L.M, f, x, r); break;
+      }
+    }
+    GBS_LAUNCH_CHECK();
+  }
+
   // out = V(f) at level l; f and out are ST vectors of that level's size.
+  // r64 / z64 (mixed forms, level 0 only): the V-cycle's FP64 input and
+  // output.  The input is rounded into f (the caller's FP32 buffer) by the
+  // first level-0 kernel, and the last level-0 sweep writes z64 in FP64,
+  // where the level's kernels allow it; otherwise separate cast passes.
   template <bool TR>
-  void cycle(size_t l, const ST* f, ST* out, cudaStream_t s) {
+  void cycle(size_t l, const ST* f, ST* out, cudaStream_t s, const double* r64 = nullptr,
+             double* z64 = nullptr) {
+    static const char* const kLevel[] = {"V-cycle level 0", "V-cycle level 1", "V-cycle level 2",
+                                         "V-cycle level 3", "V-cycle level 4", "V-cycle level 5",
+                                         "V-cycle level 6", "V-cycle level 7", "V-cycle level 8",
+                                         "V-cycle level 9+"};
+    NvtxRange range(kLevel[l < 9 ? l : 9]);
+    if (r64 && (l + 1 == lev.size() || lev[l].ilu || (TR ? npost : npre) < 1)) {
+      cast<double, ST>(lev[l].n, r64, const_cast<ST*>(f), s);   // no folding here
+      r64 = nullptr;
+    }
     if (l + 1 == lev.size()) {
       const ST* Ai = TR ? AinvT : Ainv;
       k_gemv<ST, ST, AT><<<grid_for((int64_t)nc * 32), 256, 0, s>>>(nc, Ai, f, out);
       GBS_LAUNCH_CHECK();
+      if (z64) cast<ST, double>(nc, out, z64, s);
       return;
     }
     Lev& L = lev[l];
@@ -529,11 +705,17 @@ struct DevAmg {
     const int post = TR ? npre : npost;
     ST* x = L.x;
     ST* xt = L.xt;
+    bool have_r = false;
     if (pre >= 1) {
       if (L.ilu) {
         const ST* z = ilu_apply<TR>(L, f, s);
         k_vaxpy<ST><<<grid_for(L.n), 256, 0, s>>>(L.n, (const ST*)nullptr, (ST)ilu_omega, z, x);
         GBS_LAUNCH_CHECK();
+      } else if (L.fused && !TR && pre == 1) {
+        presmooth_resid(L, f, x, L.r, s);   // x = M f and r = f - A x in one pass
+        have_r = true;
+      } else if (r64) {
+        cast_mapply<TR>(L, r64, const_cast<ST*>(f), x, s);   // f = (ST) r64 and x = M f
       } else {
         mapply<TR, VT, ST, AT>(B, nb, L.M, f, x, s);
       }
@@ -544,7 +726,7 @@ struct DevAmg {
     } else {
       GBS_CUDA(cudaMemsetAsync(x, 0, sizeof(ST) * L.n, s));
     }
-    resid<TR>(L, x, f, L.r, s);
+    if (!have_r) resid<TR>(L, x, f, L.r, s);
     Lev& Cn = lev[l + 1];
     const ST* none = nullptr;
     if (L.r_sell) sell_spmv<SPMV_SET, VT, ST, ST, AT>(L.Rs, L.r, none, Cn.f, s);
@@ -555,10 +737,30 @@ struct DevAmg {
     else if (L.p_csr) csr_spmv<SPMV_ADD, VT, ST, ST, AT>(L.Pc, Cn.e, none, x, s);
     else spmv<false, SPMV_ADD, VT, ST, ST, AT>(B, L.Pm, Cn.e, none, x, s);
     for (int it = 0; it < post; ++it) {
-      ST* dst = (it + 1 == post) ? out : xt;
+      const bool last = it + 1 == post;
+      if (last && z64 && !TR && L.a_csr && L.a_sell && !L.ilu) {
+        // the last sweep writes the FP64 output (no cast pass)
+        sell_relax<VT, ST, AT, double>(B, L.As, L.M, f, x, z64, s);
+        return;
+      }
+      ST* dst = last ? out : xt;
       sweep<TR>(L, f, x, dst, s);
       std::swap(x, xt);
     }
+    if (post == 0) GBS_CUDA(cudaMemcpyAsync(out, x, sizeof(ST) * L.n, cudaMemcpyDeviceToDevice, s));
+    if (z64) cast<ST, double>(L.n, out, z64, s);
+  }
+
+  template <bool TR>
+  void cast_mapply(Lev& L, const double* r64, ST* fin, ST* x, cudaStream_t s) {
+    const int nb = L.A.nbr;
+    switch (B) {
+      case 1: k_cast_mapply<1, TR, VT, ST, AT><<<grid_for(row_threads<1>(nb)), 256, 0, s>>>(nb, L.M, r64, fin, x); break;
+      case 2: k_cast_mapply<2, TR, VT, ST, AT><<<grid_for(row_threads<2>(nb)), 256, 0, s>>>(nb, L.M, r64, fin, x); break;
+      case 3: k_cast_mapply<3, TR, VT, ST, AT><<<grid_for(row_threads<3>(nb)), 256, 0, s>>>(nb, L.M, r64, fin, x); break;
+      case 4: k_cast_mapply<4, TR, VT, ST, AT><<<grid_for(row_threads<4>(nb)), 256, 0, s>>>(nb, L.M, r64, fin, x); break;
+    }
+    GBS_LAUNCH_CHECK();
   }
 
   // One level operation as the V-cycle runs it (measurement and tests):
@@ -582,7 +784,8 @@ struct DevAmg {
       const Lev& L = lev[l];
       const double nb = (double)L.A.nbr;
       const double nc = (double)(lev[l + 1].n / B);
-      const double Abytes = L.a_sell ? L.slots_A * (sv + 4) + 4 * (L.sl_A + 1.0)
+      const double Abytes = L.a_bsell ? L.slots_Ab * (B * B * sv + 4) + 4.0 * L.Ab.nslices * (32 / B + 1)
+                            : L.a_sell ? L.slots_A * (sv + 4) + 4 * (L.sl_A + 1.0)
                             : L.a_csr ? L.nnz_A * (sv + 4) + 4 * (L.n + 1.0)
                                       : L.nnzb_A * (B * B * sv + 4) + 4 * (nb + 1);
       const double Pbytes = L.p_sell ? L.slots_P * (sv + 4) + 4 * (L.sl_P + 1.0)
@@ -606,6 +809,15 @@ struct DevAmg {
         b += Mbytes + 2 * L.n * sx;                              // mapply (M, f, x)
         b += Abytes + Mbytes + 3 * L.n * sx;                     // relax (A, M, f, x, out)
       }
+      if (L.fused) {
+        // the fused pass (A M, f gathered, M, x and r written) replaces
+        // mapply and the residual
+        const double AMbytes = L.fused == 2
+            ? L.slots_AM * (B * B * sv + 4) + 4.0 * L.AMb.nslices * (32 / B + 1)
+            : L.slots_AM * (sv + 4) + 4 * (L.sl_AM + 1.0);
+        b -= (Mbytes + 2 * L.n * sx) + (Abytes + 3 * L.n * sx);
+        b += AMbytes + Mbytes + 3 * L.n * sx;
+      }
     }
     b += (double)nc * nc * sx + 2.0 * nc * sx;
     return b;
@@ -626,12 +838,14 @@ struct AmgPrecond final : DevPrecond {
     }
   }
   void apply(const double* r, double* z, bool tr, cudaStream_t s) override {
+    NvtxRange range("AMG preconditioner");
     if constexpr (std::is_same<ST, double>::value) {
       amg.vcycle(r, z, tr, s);
     } else {
-      cast<double, ST>(amg.n0(), r, fin, s);
-      amg.vcycle(fin, fout, tr, s);
-      cast<ST, double>(amg.n0(), fout, z, s);
+      // the precision boundary is folded into the first and the last level-0
+      // kernels where they allow it (DevAmg::cycle)
+      if (tr) amg.template cycle<true>(0, fin, fout, s, r, z);
+      else amg.template cycle<false>(0, fin, fout, s, r, z);
     }
   }
   int64_t bytes() const override { return amg.ar.bytes + ar.bytes; }
@@ -647,7 +861,15 @@ struct AmgPrecond final : DevPrecond {
   int64_t level_nnzb(int, int l) const override { return amg.lev[l].nnzb_A; }
   double bytes_per_apply() const override {
     double b = amg.bytes_per_cycle();
-    if constexpr (!std::is_same<ST, double>::value) b += amg.n0() * 2.0 * (8 + sizeof(ST));
+    if constexpr (!std::is_same<ST, double>::value) {
+      // FP64 -> ST and back; a folded side moves 4 bytes an entry more than
+      // the level-0 kernel it joins instead of a separate cast pass
+      const double n = (double)amg.n0(), sx = sizeof(ST);
+      const auto& L = amg.lev[0];
+      const bool deep = amg.lev.size() > 1 && !L.ilu;
+      b += deep && amg.npre >= 1 ? n * (8 - sx) : n * (8 + sx);
+      b += deep && L.a_csr && L.a_sell ? n * (8 - sx) : n * (8 + sx);
+    }
     return b;
   }
 };
@@ -663,40 +885,29 @@ __global__ void k_gather_u(int nn, const double* __restrict__ r, ST* __restrict_
     fu[t] = (ST)r[i * (NV + 1) + c];
   }
 }
-// q_i = r_p,i - sum_k Dblk(k) . u_{col k};  Dblk(k) = D[k] or (transposed) G[tmap k]
+// The couplings as scalar CSR of their nonzeros (on the FD stencil one
+// velocity component per neighbour block: 6 entries a pressure row of D,
+// 2 a velocity row of G, against 21 and 7 stored values on K's block
+// pattern).  Entries keep the block order, so the sums equal the block
+// kernels' above term for term.
+// q_i = r_p,i - sum_k C_k u_{col k}   (C = D, or G^T for the transposed step)
 template <int NV, class VT, class ST>
-__global__ void k_schur_q(DevBsr<VT> D, const VT* __restrict__ Dval, bool tr,
-                          const double* __restrict__ r, const ST* __restrict__ u,
-                          ST* __restrict__ q) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.nbr; i += gridDim.x * blockDim.x) {
+__global__ void k_schur_q_csr(DevCsr<VT> C, const double* __restrict__ r, const ST* __restrict__ u,
+                              ST* __restrict__ q) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C.n; i += gridDim.x * blockDim.x) {
     ST acc = ST(0);
-    for (int k = D.rp[i]; k < D.rp[i + 1]; ++k) {
-      const int j = D.col[k];
-      const int kb = tr ? D.tmap[k] : k;
-#pragma unroll
-      for (int c = 0; c < NV; ++c) acc += cvt<ST>(Dval[(size_t)kb * NV + c]) * u[(size_t)j * NV + c];
-    }
+    for (int k = C.rp[i]; k < C.rp[i + 1]; ++k) acc += cvt<ST>(C.val[k]) * u[C.col[k]];
     q[i] = (ST)r[(size_t)i * (NV + 1) + NV] - acc;
   }
 }
-// fu2[i*NV + c] = fu[i*NV + c] - sum_k Gblk(k)[c] p_{col k};  Gblk = G[k] or D[tmap k]
-template <int NV, class VT, class ST>
-__global__ void k_schur_u(DevBsr<VT> G, const VT* __restrict__ Gval, bool tr,
-                          const ST* __restrict__ fu, const ST* __restrict__ p,
-                          ST* __restrict__ fu2) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G.nbr; i += gridDim.x * blockDim.x) {
-    ST acc[NV];
-#pragma unroll
-    for (int c = 0; c < NV; ++c) acc[c] = fu[(size_t)i * NV + c];
-    for (int k = G.rp[i]; k < G.rp[i + 1]; ++k) {
-      const int j = G.col[k];
-      const int kb = tr ? G.tmap[k] : k;
-      const ST pj = p[j];
-#pragma unroll
-      for (int c = 0; c < NV; ++c) acc[c] -= cvt<ST>(Gval[(size_t)kb * NV + c]) * pj;
-    }
-#pragma unroll
-    for (int c = 0; c < NV; ++c) fu2[(size_t)i * NV + c] = acc[c];
+// fu2_t = fu_t - sum_k C_k p_{col k}   (C = G, or D^T for the transposed step)
+template <class VT, class ST>
+__global__ void k_schur_u_csr(DevCsr<VT> C, const ST* __restrict__ fu, const ST* __restrict__ p,
+                              ST* __restrict__ fu2) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < C.n; t += gridDim.x * blockDim.x) {
+    ST acc = fu[t];
+    for (int k = C.rp[t]; k < C.rp[t + 1]; ++k) acc -= cvt<ST>(C.val[k]) * p[C.col[k]];
+    fu2[t] = acc;
   }
 }
 // q_i = r_p,i (pressure part of an interleaved vector)
@@ -731,7 +942,10 @@ struct SchurPrecond final : DevPrecond {
   using ST = typename FormT<P>::ST;
   using AT = ST;
   DevAmg<P> A, S;
-  DevBsr<VT> G, D;  // share K's pattern; val = coupling values
+  // couplings as scalar CSR of their nonzeros: D (pressure rows), G
+  // (velocity rows) and, for the transposed application, G^T and D^T
+  DevCsr<VT> Dc, Gc, GcT, DcT;
+  int64_t nnz_D = 0, nnz_G = 0;
   int nv = 3, nn = 0;
   int order = 0;                 // 0 full, 1 lower
   const VT* MS = nullptr;        // pressure smoother when the pressure solve is one sweep
@@ -753,14 +967,15 @@ struct SchurPrecond final : DevPrecond {
     } else {
       S.build(HS, o, s);
     }
-    G = upload_bsr<VT, AT>(ar, Hs.G, o.tmaps, s, keep);
-    D.nbr = Hs.D.nbr;
-    D.nbc = Hs.D.nbc;
-    D.rp = G.rp;
-    D.col = G.col;
-    D.tmap = G.tmap;
-    keep.push_back(cast_vec<VT>(Hs.D.val));
-    D.val = ar.upload(keep.back().data(), keep.back().size(), s);
+    const HCsr Dh = to_scalar_csr(Hs.D), Gh = to_scalar_csr(Hs.G);
+    nnz_D = (int64_t)Dh.col.size();
+    nnz_G = (int64_t)Gh.col.size();
+    Dc = upload_csr<VT>(ar, Dh, s, keep);
+    Gc = upload_csr<VT>(ar, Gh, s, keep);
+    if (o.tmaps) {
+      GcT = upload_csr<VT>(ar, transpose(Gh), s, keep);
+      DcT = upload_csr<VT>(ar, transpose(Dh), s, keep);
+    }
     fu = ar.alloc<ST>((size_t)nn * nv);
     fu2 = ar.alloc<ST>((size_t)nn * nv);
     u1 = ar.alloc<ST>((size_t)nn * nv);
@@ -794,20 +1009,20 @@ struct SchurPrecond final : DevPrecond {
       k_gather_p<NV, ST><<<gn, 256, 0, s>>>(nn, r, q);
       GBS_LAUNCH_CHECK();
       pressure(q, p, true, s);
-      k_schur_u<NV, VT, ST><<<gn, 256, 0, s>>>(G, D.val, true, fu, p, fu2);
+      k_schur_u_csr<VT, ST><<<g, 256, 0, s>>>(DcT, fu, p, fu2);
       GBS_LAUNCH_CHECK();
       A.vcycle(fu2, u, true, s);
     } else {
       A.vcycle(fu, u1, tr, s);
       // forward: q = r_p - D u1; transposed: q = r_p - G^T u1
-      k_schur_q<NV, VT, ST><<<gn, 256, 0, s>>>(D, tr ? G.val : D.val, tr, r, u1, q);
+      k_schur_q_csr<NV, VT, ST><<<gn, 256, 0, s>>>(tr ? GcT : Dc, r, u1, q);
       GBS_LAUNCH_CHECK();
       pressure(q, p, tr, s);
       if (order == 1) {
         uout = u1;
       } else {
         // forward: fu2 = fu - G p; transposed: fu2 = fu - D^T p
-        k_schur_u<NV, VT, ST><<<gn, 256, 0, s>>>(G, tr ? D.val : G.val, tr, fu, p, fu2);
+        k_schur_u_csr<VT, ST><<<g, 256, 0, s>>>(tr ? DcT : Gc, fu, p, fu2);
         GBS_LAUNCH_CHECK();
         A.vcycle(fu2, u, tr, s);
       }
@@ -817,6 +1032,7 @@ struct SchurPrecond final : DevPrecond {
   }
 
   void apply(const double* r, double* z, bool tr, cudaStream_t s) override {
+    NvtxRange range("Schur preconditioner");
     switch (nv) {
       case 1: run<1>(r, z, tr, s); break;
       case 2: run<2>(r, z, tr, s); break;
@@ -845,10 +1061,10 @@ struct SchurPrecond final : DevPrecond {
     const double sv = sizeof(VT), sx = sizeof(ST);
     double b = (order == 1 ? 1 : 2) * A.bytes_per_cycle();
     b += MS ? nn * (sv + 2 * sx) : S.bytes_per_cycle();
-    // gather, two couplings, scatter
+    // gather, two couplings (scalar CSR of their nonzeros), scatter
     b += nn * nv * (8 + sx);
-    b += nnzb * (nv * sv + 4) + nn * nv * sx + nn * (8 + sx);
-    b += nnzb * (nv * sv + 4) + nn * sx + 2.0 * nn * nv * sx;
+    b += nnz_D * (sv + 4) + 4.0 * (nn + 1) + nn * nv * sx + nn * (8 + sx);
+    b += nnz_G * (sv + 4) + 4.0 * (nn * nv + 1) + nn * sx + 2.0 * nn * nv * sx;
     b += nn * (nv + 1) * 8 + nn * (nv + 1) * sx;
     return b;
   }

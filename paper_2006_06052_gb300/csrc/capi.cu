@@ -83,8 +83,10 @@ cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 std::vector<double> idr_shadow_space(int64_t n, int s, uint64_t seed);
 
-unsigned vgrid(int64_t n) {
-  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+// Grid of an elementwise kernel: one thread per element up to `cap` CTAs of
+// 256 threads (the device's resident CTAs, Red::cap).
+unsigned vgrid(int64_t n, int cap) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, cap));
 }
 
 HBsr from_c(const gbs_bsr* A) {
@@ -132,6 +134,8 @@ void check_params(const gbs_params* p) {
   if (p->level_format < 0 || p->level_format > 3) throw SetupError{"level_format must be 0..3"};
   if (p->schur_p < 0 || p->schur_p > 1) throw SetupError{"schur_p must be 0 or 1"};
   if (p->schur_order < 0 || p->schur_order > 1) throw SetupError{"schur_order must be 0 or 1"};
+  if (p->gmres_reorth < 0 || p->gmres_reorth > 2) throw SetupError{"gmres_reorth must be 0, 1 or 2"};
+  if (p->wait_log2 < 0 || p->wait_log2 > 40) throw SetupError{"wait_log2 must be in 0..40"};
 }
 
 AmgSetupParams amg_prm(const gbs_params* p, int relax) {
@@ -159,6 +163,7 @@ PrecondOptions pc_opts(const gbs_params* p) {
   o.schur_p_smoother = p->schur_p == 1;
   o.ilut_sweeps = p->ilut_sweeps;
   o.ilut_omega = p->ilut_omega;
+  o.wait_cycles = 1LL << p->wait_log2;
   return o;
 }
 
@@ -199,7 +204,7 @@ void alloc_work(Handle& h, cudaStream_t s) {
           }
     HSell S;
     bool sliced = false;
-    if (use_sell(c, h.B, h.prm.level_format)) {
+    if (use_sell(c, h.B, h.prm.level_format) == 1) {   // K: stencil slices only
       S = to_sell(c, h.B);
       int64_t uni = 0;
       for (int32_t ci : S.cinfo) uni += ci < 0;
@@ -210,7 +215,7 @@ void alloc_work(Handle& h, cudaStream_t s) {
       std::vector<int32_t> smap(S.src.size());
       for (size_t e = 0; e < S.src.size(); ++e) smap[e] = S.src[e] >= 0 ? map[S.src[e]] : -1;
       std::vector<std::vector<double>> keep;
-      h.Ks = upload_sell<double>(a, S, h.sc + S_ERR, s, keep);
+      h.Ks = upload_sell<double>(a, S, h.sc + S_ERR, 1LL << 31, s, keep);
       h.kcval = const_cast<double*>(h.Ks.val);
       h.kmap = a.upload(smap.data(), smap.size(), s);
       h.kmap_n = (int64_t)smap.size();
@@ -257,7 +262,12 @@ void alloc_work(Handle& h, cudaStream_t s) {
   h.ydev = a.alloc<double>(MAX_DOTS);
   GBS_CUDA(cudaMemsetAsync(h.sc, 0, sizeof(double) * S_COUNT, s));
   h.red.sc = h.sc;
-  h.red.partials = a.alloc<double>((size_t)RED_BLOCKS * MAX_DOTS);
+  // reduction partials for one wave of 256-thread CTAs on this device
+  int dev = 0, sms = 0;
+  GBS_CUDA(cudaGetDevice(&dev));
+  GBS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  h.red.cap = std::max(1, sms) * (2048 / RED_THREADS);
+  h.red.partials = a.alloc<double>((size_t)h.red.cap * MAX_DOTS);
   h.red.counter = a.alloc<unsigned>(16);
   GBS_CUDA(cudaMemsetAsync(h.red.counter, 0, sizeof(unsigned) * 16, s));
   GBS_CUDA(cudaMallocHost(&h.sc_host, sizeof(double) * S_COUNT));
@@ -274,12 +284,12 @@ void outer_B(const Handle& h, const double* x, const double* f, double* y, const
              int self_dot, int slot, int op, bool reduce, cudaStream_t s) {
   const Red& R = h.red;
 #define GBS_OUTG(BB, GG) \
-  launch_resident(k_outer<BB, GG, TR, MODE>, RED_BLOCKS, s, h.K, x, f, y, w0, self_dot, R, slot, \
+  launch_resident(k_outer<BB, GG, TR, MODE>, h.red.cap, s, h.K, x, f, y, w0, self_dot, R, slot, \
                                                                 op, reduce)
 #define GBS_OUT(BB)                                                                        \
   switch (h.K.G) {                                                                         \
     case 0:                                                                                \
-      launch_resident(k_outer_n<BB, TR, MODE>, OUTER_N_BLOCKS, s, h.K, x, f, y, w0, self_dot, R, \
+      launch_resident(k_outer_n<BB, TR, MODE>, h.red.cap / 2, s, h.K, x, f, y, w0, self_dot, R, \
                                                                   slot, op, reduce);       \
       break;                                                                               \
     case 8: GBS_OUTG(BB, 8); break;                                                        \
@@ -302,22 +312,23 @@ void outer_csr(const Handle& h, const double* x, const double* f, double* y, con
                int self_dot, int slot, int op, bool reduce, cudaStream_t s) {
   const Red& R = h.red;
   switch (h.Kc.S) {
-    case 2: launch_resident(k_outer_csr<2, MODE>, RED_BLOCKS, s, h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
-    case 4: launch_resident(k_outer_csr<4, MODE>, RED_BLOCKS, s, h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
-    case 8: launch_resident(k_outer_csr<8, MODE>, RED_BLOCKS, s, h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
-    default: launch_resident(k_outer_csr<1, MODE>, RED_BLOCKS, s, h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce);
+    case 2: launch_resident(k_outer_csr<2, MODE>, h.red.cap, s, h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
+    case 4: launch_resident(k_outer_csr<4, MODE>, h.red.cap, s, h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
+    case 8: launch_resident(k_outer_csr<8, MODE>, h.red.cap, s, h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce); break;
+    default: launch_resident(k_outer_csr<1, MODE>, h.red.cap, s, h.Kc, x, f, y, w0, self_dot, R, slot, op, reduce);
   }
   GBS_LAUNCH_CHECK();
 }
 
 void outer(const Handle& h, bool tr, int mode, const double* x, const double* f, double* y,
            const double* w0, int self_dot, int slot, int op, bool reduce, cudaStream_t s) {
+  NvtxRange range(mode == SPMV_RESID ? "outer residual" : "outer SpMV");
   if (!tr && h.k_csr && h.k_sell) {
     if (mode == SPMV_RESID)
-      launch_resident(k_outer_sell<SPMV_RESID>, RED_BLOCKS, s, h.Ks, x, f, y, w0, self_dot, h.red,
+      launch_resident(k_outer_sell<SPMV_RESID>, h.red.cap, s, h.Ks, x, f, y, w0, self_dot, h.red,
                       slot, op, (int)reduce);
     else
-      launch_resident(k_outer_sell<SPMV_SET>, RED_BLOCKS, s, h.Ks, x, f, y, w0, self_dot, h.red,
+      launch_resident(k_outer_sell<SPMV_SET>, h.red.cap, s, h.Ks, x, f, y, w0, self_dot, h.red,
                       slot, op, (int)reduce);
     GBS_LAUNCH_CHECK();
     return;
@@ -348,8 +359,9 @@ void read_scalars(Handle& h, cudaStream_t s) {
 
 // One BiCGStab iteration (all device work, no host reads).
 void bicg_iteration(Handle& h, bool tr, cudaStream_t s) {
+  NvtxRange range("BiCGStab iteration");
   const int64_t n = h.n;
-  const unsigned g = vgrid(n);
+  const unsigned g = vgrid(n, h.red.cap);
   k_bicg_p<<<g, 256, 0, s>>>(n, h.r, h.v, h.p, h.sc);
   GBS_LAUNCH_CHECK();
   h.pc->apply(h.p, h.ph, tr, s);
@@ -358,7 +370,7 @@ void bicg_iteration(Handle& h, bool tr, cudaStream_t s) {
   GBS_LAUNCH_CHECK();
   h.pc->apply(h.s, h.sh, tr, s);
   outer(h, tr, SPMV_SET, h.sh, nullptr, h.t, h.s, 1, 1, FIN_OMEGA, true, s);
-  launch_resident(k_bicg_xr, RED_BLOCKS, s, n, h.xi, h.ph, h.sh, h.s, h.t, h.r, h.rhat, h.red, 2);
+  launch_resident(k_bicg_xr, h.red.cap, s, n, h.xi, h.ph, h.sh, h.s, h.t, h.r, h.rhat, h.red, 2);
   GBS_LAUNCH_CHECK();
 }
 
@@ -426,7 +438,7 @@ gbs_status solve_bicgstab(Handle& h, const double* b, double* x, bool tr, cudaSt
   GBS_CUDA(cudaEventRecord(h.ev0, s));
   GBS_CUDA(cudaMemcpyAsync(h.bi, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   GBS_CUDA(cudaMemcpyAsync(h.xi, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  launch_resident(k_dot2, RED_BLOCKS, s, n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
+  launch_resident(k_dot2, h.red.cap, s, n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
   GBS_LAUNCH_CHECK();
   outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, 1, 4, FIN_INIT, true, s);
   GBS_CUDA(cudaMemcpyAsync(h.rhat, h.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -544,12 +556,12 @@ gbs_status solve_gmres(Handle& h, const double* b, double* x, bool tr, cudaStrea
                        gbs_info* info) {
   const int64_t n = h.n;
   const int m = h.m;
-  const unsigned g = vgrid(n);
+  const unsigned g = vgrid(n, h.red.cap);
   std::vector<double> hist;
   GBS_CUDA(cudaEventRecord(h.ev0, s));
   GBS_CUDA(cudaMemcpyAsync(h.bi, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   GBS_CUDA(cudaMemcpyAsync(h.xi, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  launch_resident(k_dot2, RED_BLOCKS, s, n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
+  launch_resident(k_dot2, h.red.cap, s, n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
   GBS_LAUNCH_CHECK();
   read_scalars(h, s);
   const double bb = h.sc_host[S_BB];
@@ -585,19 +597,24 @@ gbs_status solve_gmres(Handle& h, const double* b, double* x, bool tr, cudaStrea
     gv[0] = beta;
     int j = 0;
     while (j < m && it < h.prm.maxiter) {
+      NvtxRange step("GMRES Arnoldi step");
       double* w = h.V + (size_t)(j + 1) * n;
       h.pc->apply(h.V + (size_t)j * n, h.z, tr, s);
       outer(h, tr, SPMV_SET, h.z, nullptr, w, nullptr, 0, 0, FIN_STORE, false, s);
       const int J = j + 1;
-      launch_resident(k_multidot, RED_BLOCKS, s, n, h.V, J, w, h.hcol, h.red, 5, nullptr);
+      NvtxRange orth("GMRES orthogonalisation");
+      launch_resident(k_multidot, h.red.cap, s, n, h.V, J, w, h.hcol, h.red, 5, nullptr);
       GBS_LAUNCH_CHECK();
-      launch_resident(k_orth, RED_BLOCKS, s, n, h.V, J, w, h.hcol, nullptr, h.red, 6, nullptr);
+      launch_resident(k_orth, h.red.cap, s, n, h.V, J, w, h.hcol, nullptr, h.red, 6, nullptr);
       GBS_LAUNCH_CHECK();
-      const double* gate = h.sc + S_REORTH;
-      launch_resident(k_multidot, RED_BLOCKS, s, n, h.V, J, w, h.hcol2, h.red, 7, gate);
-      GBS_LAUNCH_CHECK();
-      launch_resident(k_orth, RED_BLOCKS, s, n, h.V, J, w, h.hcol2, h.hcol, h.red, 8, gate);
-      GBS_LAUNCH_CHECK();
+      if (h.prm.gmres_reorth != 0) {
+        // the second pass: always, or when k_orth flagged a drop of ||w||
+        const double* gate = h.prm.gmres_reorth == 2 ? nullptr : h.sc + S_REORTH;
+        launch_resident(k_multidot, h.red.cap, s, n, h.V, J, w, h.hcol2, h.red, 7, gate);
+        GBS_LAUNCH_CHECK();
+        launch_resident(k_orth, h.red.cap, s, n, h.V, J, w, h.hcol2, h.hcol, h.red, 8, gate);
+        GBS_LAUNCH_CHECK();
+      }
       k_normalize<<<g, 256, 0, s>>>(n, w, h.sc, h.hcol + J);
       GBS_LAUNCH_CHECK();
       GBS_CUDA(cudaMemcpyAsync(h.h_host, h.hcol, sizeof(double) * (J + 1), cudaMemcpyDeviceToHost, s));
@@ -674,12 +691,12 @@ gbs_status solve_idrs(Handle& h, const double* b, double* x, bool tr, cudaStream
                       gbs_info* info) {
   const int64_t n = h.n;
   const int sd = h.prm.idr_s;
-  const unsigned g = vgrid(n);
+  const unsigned g = vgrid(n, h.red.cap);
   std::vector<double> hist;
   GBS_CUDA(cudaEventRecord(h.ev0, s));
   GBS_CUDA(cudaMemcpyAsync(h.bi, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   GBS_CUDA(cudaMemcpyAsync(h.xi, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  launch_resident(k_dot2, RED_BLOCKS, s, n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
+  launch_resident(k_dot2, h.red.cap, s, n, h.bi, h.bi, nullptr, h.red, 3, FIN_BB);
   GBS_LAUNCH_CHECK();
   outer(h, tr, SPMV_RESID, h.xi, h.bi, h.r, nullptr, 1, 4, FIN_RR, true, s);
   read_scalars(h, s);
@@ -719,7 +736,7 @@ gbs_status solve_idrs(Handle& h, const double* b, double* x, bool tr, cudaStream
     return rel <= h.prm.tol;
   };
   auto multidot_P = [&](const double* w, std::vector<double>& out) {
-    launch_resident(k_multidot, RED_BLOCKS, s, n, h.Pidr, sd, w, h.hcol, h.red, 5, nullptr);
+    launch_resident(k_multidot, h.red.cap, s, n, h.Pidr, sd, w, h.hcol, h.red, 5, nullptr);
     GBS_LAUNCH_CHECK();
     GBS_CUDA(cudaMemcpyAsync(h.h_host, h.hcol, sizeof(double) * sd, cudaMemcpyDeviceToHost, s));
     GBS_CUDA(cudaStreamSynchronize(s));
@@ -771,7 +788,7 @@ gbs_status solve_idrs(Handle& h, const double* b, double* x, bool tr, cudaStream
         break;
       }
       const double beta = f[k] / MM(k, k);
-      launch_resident(k_idr_update, RED_BLOCKS, s, n, h.r, h.xi, Gk, Uk, beta, h.red, 4);
+      launch_resident(k_idr_update, h.red.cap, s, n, h.r, h.xi, Gk, Uk, beta, h.red, 4);
       GBS_LAUNCH_CHECK();
       const double res = rownorm();
       if (!std::isfinite(res)) {
@@ -800,7 +817,7 @@ gbs_status solve_idrs(Handle& h, const double* b, double* x, bool tr, cudaStream
       breakdown = true;
       break;
     }
-    launch_resident(k_idr_update, RED_BLOCKS, s, n, h.r, h.xi, h.t, h.ph, om, h.red, 4);
+    launch_resident(k_idr_update, h.red.cap, s, n, h.r, h.xi, h.t, h.ph, om, h.red, 4);
     GBS_LAUNCH_CHECK();
     const double res = rownorm();
     if (confirm(res)) conv = true;
@@ -978,6 +995,8 @@ gbs_status gbs_params_default(gbs_params* p) {
   p->ilut_tau = 1e-2;
   p->ilut_sweeps = 2;
   p->ilut_omega = 1.0;
+  p->gmres_reorth = 0;
+  p->wait_log2 = 31;
   return GBS_OK;
 }
 
@@ -1136,11 +1155,11 @@ gbs_status gbs_update_values(gbs_hierarchy* hh, const double* vals, void* stream
                              cudaMemcpyDeviceToDevice, s));
     if (h.k_csr) {
       if (h.k_sell)
-        k_gather_sell<<<vgrid(h.kmap_n), 256, 0, s>>>(h.kmap_n, h.kmap, h.Kval, h.kcval);
+        k_gather_sell<<<vgrid(h.kmap_n, h.red.cap), 256, 0, s>>>(h.kmap_n, h.kmap, h.Kval, h.kcval);
       else
-        k_gather_vals<<<vgrid((int64_t)h.Kh.val.size()), 256, 0, s>>>(h.kmap_n, h.kmap, h.Kval, h.kcval);
+        k_gather_vals<<<vgrid((int64_t)h.Kh.val.size(), h.red.cap), 256, 0, s>>>(h.kmap_n, h.kmap, h.Kval, h.kcval);
       GBS_LAUNCH_CHECK();
-      k_check_outside<<<vgrid((int64_t)h.Kh.val.size()), 256, 0, s>>>((int64_t)h.Kh.val.size(), h.kzero,
+      k_check_outside<<<vgrid((int64_t)h.Kh.val.size(), h.red.cap), 256, 0, s>>>((int64_t)h.Kh.val.size(), h.kzero,
                                                                       h.Kval, h.kflag);
       GBS_LAUNCH_CHECK();
       h.k_check_pending = true;

@@ -8,6 +8,10 @@
 #include <string>
 #include <vector>
 
+#include <cstdlib>
+
+#include <nvtx3/nvToolsExt.h>
+
 #include "setup.hpp"
 
 namespace gbs {
@@ -93,6 +97,7 @@ struct PrecondOptions {
   int schur_order = 0;   // 0 full (two velocity solves), 1 lower (one)
   bool schur_p_smoother = false;  // pressure solve = one smoother application (HSchur::MS)
   double* err = nullptr;          // device slot a timed-out pipelined kernel sets to 1.0
+  long long wait_cycles = 1LL << 31;  // bound of a pipeline wait (SM clocks)
   int ilut_sweeps = 2;            // Jacobi sweeps per ILUT triangular solve
   double ilut_omega = 1.0;        // ILUT relaxation damping
 };
@@ -112,5 +117,27 @@ std::unique_ptr<DevPrecond> make_schur_fp32(const HSchur&, const HAmg&, const HA
                                             const PrecondOptions&, cudaStream_t);
 std::unique_ptr<DevPrecond> make_schur_bf16(const HSchur&, const HAmg&, const HAmg&,
                                             const PrecondOptions&, cudaStream_t);
+
+// NVTX ranges around each Krylov phase and each V-cycle level, for
+// profilers that show them; recorded only when the environment variable
+// GBS_NVTX is set (to anything but 0) when the library first checks it.
+inline bool nvtx_on() {
+  static const bool on = [] {
+    const char* e = std::getenv("GBS_NVTX");
+    return e && e[0] && e[0] != '0';
+  }();
+  return on;
+}
+struct NvtxRange {
+  bool on;
+  explicit NvtxRange(const char* name) : on(nvtx_on()) {
+    if (on) nvtxRangePushA(name);
+  }
+  ~NvtxRange() {
+    if (on) nvtxRangePop();
+  }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace gbs

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace gbs {
 
 template <class VT>
@@ -55,10 +57,33 @@ struct DevSell {
   const int* col = nullptr;
   const VT* val = nullptr;
   double* err = nullptr;      // set to 1.0 by a kernel whose pipeline wait timed out
+  long long wait = 1LL << 31; // bound of a pipeline wait, in SM clocks
   // uniform slices (HSell): cinfo[q] < 0, and entry k of lane i sits at
   // column row_i + uinfo[-1 - cinfo[q] + k].x when bit i of .y is set
   const int* cinfo = nullptr;
   const int2* uinfo = nullptr;
+  bool uniform = false;       // every slice is uniform (a stencil operator)
+  const int* node = nullptr;  // sorted form: node of each slot (-1: none); null: natural
+};
+
+// Node of lane `lane` of 32-node group g of a sliced operator, -1 if none.
+template <class VT>
+__device__ __forceinline__ int64_t sell_node(const DevSell<VT>& A, int64_t g, int lane) {
+  const int64_t p = g * 32 + lane;
+  if (A.node) return __ldg(A.node + p);
+  return p < A.n / A.B ? p : -1;
+}
+
+// Block-row slices of a block level (HBSell): slice q holds R = 32 / B
+// block rows, slot i of the slice is block row perm[q * R + i] (-1: none),
+// and entry k of slot i is block (off[q] + k) * R + i.
+template <class VT>
+struct DevBSell {
+  int nbr = 0, nslices = 0;
+  const int* perm = nullptr;
+  const int* off = nullptr;
+  const int* col = nullptr;
+  const VT* val = nullptr;
 };
 
 // Lanes per scalar CSR row.  Short rows keep one lane per row: that lane
@@ -582,6 +607,203 @@ __global__ void __launch_bounds__(256, 4) k_relax(DevBsr<VT> A, const VT* __rest
   xo[o] = (XT)out;
 }
 
+// ------------------------------------------------------- block-row slices
+// One warp per slice, one lane per scalar row: lane (slot, r) sums row r of
+// its slot's blocks.  The rows of a slice have nearly equal lengths (sorted
+// at setup), so few lanes idle, and no lane shares a row, so there are no
+// cross-lane sums: every FP64 instruction is an FMA of the product.  Entry
+// k of the slice's R slots is R consecutive blocks, so a warp's value load
+// reads R * B * B contiguous values.
+// Loads in issue order (volatile PTX keeps them in program order, so a
+// batch of entries puts all its loads in flight before the first use; the
+// compiler otherwise sinks each load to its use -- measured on the FP64
+// block slices: 38 long-scoreboard stalls per issue, FP64 pipe 78% busy).
+__device__ __forceinline__ int ld_nc_s32(const int* p) {
+  int v;
+  asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_nc_f64(const double* p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_cs_f64(const double* p) {
+  double v;
+  asm volatile("ld.global.cs.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void ld_nc_v2f64(const double* p, double& a, double& b) {
+  asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(p));
+}
+__device__ __forceinline__ void ld_cs_v2f64(const double* p, double& a, double& b) {
+  asm volatile("ld.global.cs.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(p));
+}
+// B consecutive doubles at p (16-byte aligned when B is even).
+template <int B, bool CS>
+__device__ __forceinline__ void ld_run_f64(const double* p, double (&o)[B]) {
+  if constexpr (B % 2 == 0) {
+#pragma unroll
+    for (int e = 0; e < B; e += 2) {
+      if constexpr (CS) ld_cs_v2f64(p + e, o[e], o[e + 1]);
+      else ld_nc_v2f64(p + e, o[e], o[e + 1]);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < B; ++e) o[e] = CS ? ld_cs_f64(p + e) : ld_nc_f64(p + e);
+  }
+}
+
+// FP64 block slices: row r of slot `slot` of slice q times x, in batches of
+// U entries whose column, value and x loads all issue before the FMAs.  U
+// keeps the kernels within 64 registers, so that every slice's warp is
+// resident at once on the levels that take slices (4 CTAs of 256 threads
+// per SM; without a minimum the compiler caps them at 32 registers and
+// serialises the loads).
+template <int B>
+__device__ __forceinline__ double bsell_row_dot_f64(const int* __restrict__ off,
+                                                    const int* __restrict__ col,
+                                                    const double* __restrict__ val,
+                                                    const double* __restrict__ x, int q, int slot,
+                                                    int r) {
+  constexpr int R = 32 / B;
+  constexpr int U = B >= 3 ? 2 : 8 / B;
+  const int k0 = __ldg(off + q), w = __ldg(off + q + 1) - k0;
+  const int* __restrict__ c = col + (size_t)k0 * R + slot;
+  const double* __restrict__ v = val + ((size_t)k0 * R + slot) * (B * B) + r * B;
+  double acc = 0.0;
+  for (int k = 0; k < w; k += U) {
+    int j[U];
+    double a[U][B], xv[U][B];
+#pragma unroll
+    for (int u = 0; u < U; ++u) j[u] = ld_nc_s32(c + (size_t)min(k + u, w - 1) * R);
+#pragma unroll
+    for (int u = 0; u < U; ++u) ld_run_f64<B, true>(v + (size_t)min(k + u, w - 1) * (R * B * B), a[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) ld_run_f64<B, false>(x + (size_t)j[u] * B, xv[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (k + u < w) {
+#pragma unroll
+        for (int cc = 0; cc < B; ++cc) acc += a[u][cc] * xv[u][cc];
+      }
+  }
+  return acc;
+}
+
+template <int B, class VT, class XT, class AT>
+__device__ __forceinline__ AT bsell_row_dot(const DevBSell<VT>& A, const XT* __restrict__ x, int q,
+                                            int slot, int r) {
+  constexpr int R = 32 / B;
+  const int k0 = __ldg(A.off + q), w = __ldg(A.off + q + 1) - k0;
+  const int* __restrict__ c = A.col + (size_t)k0 * R + slot;
+  const VT* __restrict__ v = A.val + ((size_t)k0 * R + slot) * (B * B) + r * B;
+  AT acc = AT(0);
+  if constexpr (std::is_same<VT, double>::value && std::is_same<XT, double>::value) {
+    return bsell_row_dot_f64<B>(A.off, A.col, A.val, x, q, slot, r);
+  }
+  // U entries per batch: all column and value loads of a batch issue before
+  // the dependent x gathers.  Entries past the slice's width re-read its
+  // last entry and are dropped at the FMA (w is warp-uniform: no divergence).
+  constexpr int U = 4;
+  for (int k = 0; k < w; k += U) {
+    int j[U];
+    AT a[U][B];
+#pragma unroll
+    for (int u = 0; u < U; ++u) j[u] = __ldg(c + (size_t)min(k + u, w - 1) * R);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      load_run<B, VT, AT, true>(v + (size_t)min(k + u, w - 1) * (R * B * B), a[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      AT xv[B];
+      load_run<B, XT, AT, false>(x + (size_t)j[u] * B, xv);
+      if (k + u < w) {
+#pragma unroll
+        for (int cc = 0; cc < B; ++cc) acc += a[u][cc] * xv[cc];
+      }
+    }
+  }
+  return acc;
+}
+
+// MODE SET / RESID / ADD on a level in block-row slices.
+template <int B, int MODE, class VT, class XT, class YT, class AT>
+__global__ void __launch_bounds__(256, 4) k_bsell_spmv(DevBSell<VT> A, const XT* __restrict__ x,
+                                                     const YT* __restrict__ f, YT* __restrict__ y) {
+  constexpr int R = 32 / B;
+  const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (q >= A.nslices) return;
+  const int lane = threadIdx.x & 31;
+  const int slot = lane / B, r = lane - slot * B;
+  if (slot >= R) return;   // B = 3: lanes 30 and 31 hold no row
+  const int row = __ldg(A.perm + q * R + slot);
+  const AT acc = bsell_row_dot<B, VT, XT, AT>(A, x, (int)q, slot, r);
+  if (row < 0) return;
+  const size_t o = (size_t)row * B + r;
+  if constexpr (MODE == SPMV_SET) y[o] = (YT)acc;
+  else if constexpr (MODE == SPMV_RESID) y[o] = (YT)(cvt<AT>(f[o]) - acc);
+  else y[o] = (YT)(cvt<AT>(y[o]) + acc);
+}
+
+// xo = x + M (f - A x) on a level in block-row slices: the B lanes of a
+// slot exchange their residuals by shuffles for the B x B block of M.
+template <int B, class VT, class XT, class AT>
+__global__ void __launch_bounds__(256, 4) k_bsell_relax(DevBSell<VT> A, const VT* __restrict__ M,
+                                                      const XT* __restrict__ f,
+                                                      const XT* __restrict__ x,
+                                                      XT* __restrict__ xo) {
+  constexpr int R = 32 / B;
+  const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (q >= A.nslices) return;   // warp-uniform
+  const int lane = threadIdx.x & 31;
+  const int slot0 = lane / B;
+  const bool lane_ok = slot0 < R;
+  const int slot = lane_ok ? slot0 : R - 1;   // B = 3: lanes 30, 31 shadow slot R - 1
+  const int r = lane_ok ? lane - slot * B : 0;
+  const int row = __ldg(A.perm + q * R + slot);
+  const AT acc = bsell_row_dot<B, VT, XT, AT>(A, x, (int)q, slot, r);
+  const size_t o = (size_t)(row < 0 ? 0 : row) * B + r;
+  const AT res = row >= 0 ? cvt<AT>(f[o]) - acc : AT(0);
+  AT rb[B];
+#pragma unroll
+  for (int c = 0; c < B; ++c) rb[c] = __shfl_sync(0xffffffffu, res, slot * B + c);
+  if (!lane_ok || row < 0) return;
+  AT mr[B];
+  load_run<B, VT, AT, false>(M + (size_t)row * (B * B) + r * B, mr);
+  AT out = cvt<AT>(x[o]);
+#pragma unroll
+  for (int c = 0; c < B; ++c) out += mr[c] * rb[c];
+  xo[o] = (XT)out;
+}
+
+// Zero-guess pre-smoothing step fused with the residual on a level in
+// block-row slices: x = M f and r = f - (A M) f (AM = A M precomputed on
+// the slices).  Each lane forms its own row of both outputs; no shuffles.
+template <int B, class VT, class XT, class AT>
+__global__ void __launch_bounds__(256, 4) k_bsell_presmooth(DevBSell<VT> AM, const VT* __restrict__ M,
+                                                          const XT* __restrict__ f,
+                                                          XT* __restrict__ x, XT* __restrict__ r) {
+  constexpr int R = 32 / B;
+  const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (q >= AM.nslices) return;
+  const int lane = threadIdx.x & 31;
+  const int slot = lane / B, rr = lane - slot * B;
+  if (slot >= R) return;
+  const int row = __ldg(AM.perm + q * R + slot);
+  const AT acc = bsell_row_dot<B, VT, XT, AT>(AM, f, (int)q, slot, rr);
+  if (row < 0) return;
+  AT fv[B], mr[B];
+  load_run<B, XT, AT, false>(f + (size_t)row * B, fv);
+  load_run<B, VT, AT, false>(M + (size_t)row * (B * B) + rr * B, mr);
+  AT xo = AT(0);
+#pragma unroll
+  for (int c = 0; c < B; ++c) xo += mr[c] * fv[c];
+  const size_t o = (size_t)row * B + rr;
+  x[o] = (XT)xo;
+  r[o] = (XT)(cvt<AT>(f[o]) - acc);
+}
+
 // ------------------------------------------------------- scalar CSR levels
 template <int S, class VT, class XT, class AT>
 __device__ __forceinline__ AT csr_row_dot(const DevCsr<VT>& A, const XT* __restrict__ x, int row,
@@ -649,6 +871,31 @@ __global__ void __launch_bounds__(256, 4) k_mapply(int nbr, const VT* __restrict
 #pragma unroll
   for (int c = 0; c < B; ++c) out += mr[c] * fv[c];
   x[(size_t)m.brow * B + m.r] = (XT)out;
+}
+
+// The zero-guess smoothing step of a mixed form's finest level with the
+// FP64 -> FP32 precision boundary folded in: fin = (XT) r, rounded to
+// nearest even as the separate cast would, and x = M fin (M^T when TR),
+// in one pass over r.
+template <int B, bool TR, class VT, class XT, class AT>
+__global__ void __launch_bounds__(256, 4) k_cast_mapply(int nbr, const VT* __restrict__ M,
+                                                     const double* __restrict__ r,
+                                                     XT* __restrict__ fin, XT* __restrict__ x) {
+  RowMap<B> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  if (!m.lane_ok || m.brow >= nbr) return;
+  double rv[B];
+  load_run<B, double, double, false>(r + (size_t)m.brow * B, rv);
+  AT fv[B], mr[B];
+#pragma unroll
+  for (int c = 0; c < B; ++c) fv[c] = cvt<AT>((XT)rv[c]);
+  if constexpr (!TR) load_run<B, VT, AT, false>(M + (size_t)m.brow * (B * B) + m.r * B, mr);
+  else load_col<B, VT, AT>(M + (size_t)m.brow * (B * B), m.r, mr);
+  AT out = AT(0);
+#pragma unroll
+  for (int c = 0; c < B; ++c) out += mr[c] * fv[c];
+  const size_t o = (size_t)m.brow * B + m.r;
+  fin[o] = (XT)r[o];
+  x[o] = (XT)out;
 }
 
 // x = Ainv f, dense n x n row-major, one warp per row.

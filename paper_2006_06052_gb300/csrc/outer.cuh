@@ -1,7 +1,7 @@
 // FP64 outer-Krylov kernels: SpMV of K with fused dot products,
 // BiCGStab vector updates, GMRES orthogonalisation, sampled outer
 // product.  Dots use a deterministic two-level reduction: a fixed grid of
-// at most RED_BLOCKS blocks (all resident at once), warp-shuffle +
+// at most Red::cap blocks (all resident at once), warp-shuffle +
 // shared-memory tree per block, then
 // the last block to finish sums the per-block partials in block order
 // and runs a scalar epilogue ("finalize") on thread 0.  No result depends
@@ -19,8 +19,10 @@
 namespace gbs {
 
 constexpr int RED_THREADS = 256;
-constexpr int RED_BLOCKS = 152 * 8;   // 8 CTAs of 256 threads per SM: full occupancy
-constexpr int OUTER_N_BLOCKS = 152 * 4;  // one-lane-per-row FP64 SpMV: FP64-pipe bound, half occupancy is faster
+// The allocation-free entry point's fixed grid: 4 CTAs per SM of GB300's
+// 152 (one-lane-per-row FP64 SpMV: FP64-pipe bound, half occupancy is
+// faster).  A handle sizes its own grids from the device (Red::cap).
+constexpr int OUTER_N_BLOCKS = 152 * 4;
 constexpr int MAX_DOTS = 72;   // GMRES multi-dot: up to 64 basis vectors + spares
 
 enum ScalarSlot {
@@ -50,7 +52,8 @@ inline void launch_resident(void (*fn)(KA...), int cap, cudaStream_t s, A&&... a
 }
 
 struct Red {
-  double* partials;   // RED_BLOCKS * MAX_DOTS
+  int cap = 1;        // CTAs of a reduction grid: 8 per SM of this device (one wave)
+  double* partials;   // cap * MAX_DOTS
   unsigned* counter;  // one per reduction slot; reset by the last block
   double* sc;
 };
@@ -251,9 +254,10 @@ __global__ void __launch_bounds__(RED_THREADS, 4)
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < K.nslices; q += nw) {
     const int64_t g = q / K.B;
-    const int64_t row = (g * 32 + lane) * K.B + (q - g * K.B);
+    const int64_t node = sell_node(K, g, lane);
+    const int64_t row = (node < 0 ? 0 : node) * K.B + (q - g * K.B);
     const double acc = sell_row_dot_direct<double, double, double>(K, x, (int)q, lane, row);
-    if (row < K.n) {
+    if (node >= 0) {
       const double val = MODE == SPMV_RESID ? f[row] - acc : acc;
       y[row] = val;
       if (w0) d[0] += val * w0[row];

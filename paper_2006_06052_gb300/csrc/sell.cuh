@@ -112,13 +112,35 @@ __device__ __forceinline__ bool bar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Non-blocking test of the phase with parity `parity`.
+__device__ __forceinline__ bool bar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 constexpr long long WAIT_CYCLES = 1LL << 31;   // about a second at 2 GHz
-// Wait for the phase with parity `parity` to complete; false on timeout.
-__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity) {
-  if (bar_try(b, parity)) return true;
+constexpr long long WAIT_POLL = 1LL << 20;     // bounds below this poll without suspending
+// Wait for the phase with parity `parity` to complete; false after `bound`
+// SM clocks.  try_wait may suspend the thread for a while by itself, so a
+// bound below WAIT_POLL (tests of the timeout path) polls with test_wait,
+// which returns at once, and is honoured to the clock.
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity,
+                                         long long bound = WAIT_CYCLES) {
   const long long t0 = clock64();
+  if (bound < WAIT_POLL) {
+    while (!bar_test(b, parity))
+      if (clock64() - t0 > bound) return false;
+    return true;
+  }
+  if (bar_try(b, parity)) return true;
   while (!bar_try(b, parity))
-    if (clock64() - t0 > WAIT_CYCLES) return false;
+    if (clock64() - t0 > bound) return false;
   return true;
 }
 
@@ -198,8 +220,10 @@ __device__ __forceinline__ bool sell_pipe(const DevSell<VT>& A, const XT* __rest
     const int o0 = __ldg(A.off + q), w = __ldg(A.off + q + 1) - o0;
     const int nc = min(CW, w - ck);
     // the decision to stop is warp-uniform: every lane takes it together
-    if (!__all_sync(0xffffffffu, bar_wait(&sm.bar[st], (uint32_t)(it / NST) & 1u))) {
+    if (!__all_sync(0xffffffffu, bar_wait(&sm.bar[st], (uint32_t)(it / NST) & 1u, A.wait))) {
       if (lane == 0 && A.err) *A.err = 1.0;
+      // every copy in flight lands before the warp leaves: the drain waits
+      // with the full bound whatever A.wait is
       for (int j = it; j < issued; ++j)
         (void)bar_wait(&sm.bar[j % NST], (uint32_t)(j / NST) & 1u);
       __syncwarp();
@@ -250,8 +274,9 @@ __global__ void __launch_bounds__(SELL_WARPS * 32, 2)
   const int lane = threadIdx.x & 31;
   sell_pipe<VT, XT, AT>(A, x, 1, A.nslices, sm, [&](int64_t q, int, AT acc) {
     const int64_t g = q / A.B;
-    const int64_t row = (g * 32 + lane) * A.B + (q - g * A.B);
-    if (row >= A.n) return;
+    const int64_t node = sell_node(A, g, lane);
+    if (node < 0) return;
+    const int64_t row = node * A.B + (q - g * A.B);
     if constexpr (MODE == SPMV_SET) y[row] = (YT)acc;
     else if constexpr (MODE == SPMV_RESID) y[row] = (YT)(cvt<AT>(f[row]) - acc);
     else y[row] = (YT)(cvt<AT>(y[row]) + acc);
@@ -260,10 +285,10 @@ __global__ void __launch_bounds__(SELL_WARPS * 32, 2)
 
 // xo = x + M (f - A x): one unit is a group of 32 nodes (its B slices), so
 // each lane ends with the whole residual of its node for the B x B block.
-template <int B, class VT, class XT, class AT>
+template <int B, class VT, class XT, class AT, class OT = XT>
 __global__ void __launch_bounds__(SELL_WARPS * 32, 2)
     k_sell_relax(DevSell<VT> A, const VT* __restrict__ M, const XT* __restrict__ f,
-                 const XT* __restrict__ x, XT* __restrict__ xo) {
+                 const XT* __restrict__ x, OT* __restrict__ xo) {
   extern __shared__ __align__(128) unsigned char sell_smem[];
   SellStages<VT>& sm = reinterpret_cast<SellStages<VT>*>(sell_smem)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
@@ -274,8 +299,8 @@ __global__ void __launch_bounds__(SELL_WARPS * 32, 2)
     for (int r = 0; r < B; ++r)
       if (r == c) res[r] = acc;
     if (c != B - 1) return;
-    const int64_t node = g * 32 + lane;
-    if (node >= nn) return;
+    const int64_t node = sell_node(A, g, lane);
+    if (node < 0) return;
     AT fv[B], xv[B];
     load_run<B, XT, AT, false>(f + node * B, fv);
     load_run<B, XT, AT, false>(x + node * B, xv);
@@ -288,7 +313,7 @@ __global__ void __launch_bounds__(SELL_WARPS * 32, 2)
       AT out = xv[r];
 #pragma unroll
       for (int c2 = 0; c2 < B; ++c2) out += mr[c2] * res[c2];
-      xo[node * B + r] = (XT)out;
+      xo[node * B + r] = (OT)(XT)out;
     }
   });
 }
@@ -300,6 +325,10 @@ __global__ void __launch_bounds__(SELL_WARPS * 32, 2)
 // (C2 V-cycle 379 us staged, 358 us direct).  The direct kernels load each
 // column straight from global memory, four columns in flight per lane, at
 // up to 32 warps per SM.
+//
+// (Measured alternative that lost: each lane loading one column's offset
+// and mask once and the warp broadcasting them by shuffles, in batches of
+// 8 columns -- C2 outer SpMV 43.7 us against 38.3.)
 template <class VT, class XT, class AT>
 __device__ __forceinline__ AT sell_row_dot_direct(const DevSell<VT>& A, const XT* __restrict__ x, int q,
                                                   int lane, int64_t row) {
@@ -334,28 +363,30 @@ __global__ void __launch_bounds__(256, 4) k_sell_spmv_direct(DevSell<VT> A, cons
   if (q >= A.nslices) return;
   const int lane = threadIdx.x & 31;
   const int g = (int)(q / A.B), c = (int)(q - (int64_t)g * A.B);
-  const int64_t row = ((int64_t)g * 32 + lane) * A.B + c;
+  const int64_t node = sell_node(A, g, lane);
+  const int64_t row = (node < 0 ? 0 : node) * A.B + c;   // no entries in an empty lane
   const AT acc = sell_row_dot_direct<VT, XT, AT>(A, x, (int)q, lane, row);
-  if (row >= A.n) return;
+  if (node < 0) return;
   if constexpr (MODE == SPMV_SET) y[row] = (YT)acc;
   else if constexpr (MODE == SPMV_RESID) y[row] = (YT)(cvt<AT>(f[row]) - acc);
   else y[row] = (YT)(cvt<AT>(y[row]) + acc);
 }
-template <int B, class VT, class XT, class AT>
+template <int B, class VT, class XT, class AT, class OT = XT>
 __global__ void __launch_bounds__(256, 4) k_sell_relax_direct(DevSell<VT> A, const VT* __restrict__ M,
                                                          const XT* __restrict__ f,
                                                          const XT* __restrict__ x,
-                                                         XT* __restrict__ xo) {
+                                                         OT* __restrict__ xo) {
   const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int nn = A.n / B;
   if (g * 32 >= nn) return;
   const int lane = threadIdx.x & 31;
-  const int64_t node = g * 32 + lane;
+  const int64_t node = sell_node(A, g, lane);
+  const int64_t nd = node < 0 ? 0 : node;   // no entries in an empty lane
   AT res[B];
 #pragma unroll
   for (int c = 0; c < B; ++c)
-    res[c] = sell_row_dot_direct<VT, XT, AT>(A, x, (int)(g * B + c), lane, node * B + c);
-  if (node >= nn) return;
+    res[c] = sell_row_dot_direct<VT, XT, AT>(A, x, (int)(g * B + c), lane, nd * B + c);
+  if (node < 0) return;
   AT fv[B], xv[B];
   load_run<B, XT, AT, false>(f + node * B, fv);
   load_run<B, XT, AT, false>(x + node * B, xv);
@@ -368,9 +399,45 @@ __global__ void __launch_bounds__(256, 4) k_sell_relax_direct(DevSell<VT> A, con
     AT out = xv[r];
 #pragma unroll
     for (int c = 0; c < B; ++c) out += mr[c] * res[c];
-    xo[node * B + r] = (XT)out;
+    xo[node * B + r] = (OT)(XT)out;
   }
 }
+// Zero-guess pre-smoothing step fused with the residual (FP64 forms):
+// x = M f and r = f - A x = f - (A M) f, with AM = A M precomputed on the
+// level's slices, so no kernel has to wait for x.  One warp per 32-node
+// group as in k_sell_relax_direct; each lane ends with its node's B rows
+// of (A M) f and forms both outputs.
+template <int B, class VT, class XT, class AT>
+__global__ void __launch_bounds__(256, 4) k_sell_presmooth_direct(DevSell<VT> AM,
+                                                             const VT* __restrict__ M,
+                                                             const XT* __restrict__ f,
+                                                             XT* __restrict__ x,
+                                                             XT* __restrict__ r) {
+  const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int nn = AM.n / B;
+  if (g * 32 >= nn) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t node = sell_node(AM, g, lane);
+  const int64_t nd = node < 0 ? 0 : node;   // no entries in an empty lane
+  AT amf[B];
+#pragma unroll
+  for (int c = 0; c < B; ++c)
+    amf[c] = sell_row_dot_direct<VT, XT, AT>(AM, f, (int)(g * B + c), lane, nd * B + c);
+  if (node < 0) return;
+  AT fv[B];
+  load_run<B, XT, AT, false>(f + node * B, fv);
+#pragma unroll
+  for (int rr = 0; rr < B; ++rr) {
+    AT mr[B];
+    load_run<B, VT, AT, false>(M + node * (B * B) + rr * B, mr);
+    AT xo = AT(0);
+#pragma unroll
+    for (int c = 0; c < B; ++c) xo += mr[c] * fv[c];
+    x[node * B + rr] = (XT)xo;
+    r[node * B + rr] = (XT)(fv[rr] - amf[rr]);
+  }
+}
+
 // Persistent pipelined launch: dynamic shared memory for the stages, as
 // many CTAs as stay resident, at most cap.
 template <class... KA, class... A>

@@ -512,6 +512,26 @@ HSchur schur_split(const HBsr& K, int nvel) {
   return S;
 }
 
+HBsr scale_columns(const HBsr& A, const std::vector<double>& M) {
+  if (A.br != A.bc) fail("scale_columns needs square blocks");
+  const int B = A.br, bs = B * B;
+  if ((int64_t)M.size() != (int64_t)A.nbc * bs) fail("scale_columns: M has the wrong size");
+  HBsr C = A;
+  for (int i = 0; i < A.nbr; ++i)
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      const double* a = &A.val[(size_t)k * bs];
+      const double* m = &M[(size_t)A.col[k] * bs];
+      double* c = &C.val[(size_t)k * bs];
+      for (int r = 0; r < B; ++r)
+        for (int cc = 0; cc < B; ++cc) {
+          double acc = 0.0;
+          for (int t = 0; t < B; ++t) acc += a[r * B + t] * m[t * B + cc];
+          c[r * B + cc] = acc;
+        }
+    }
+  return C;
+}
+
 HCsr to_scalar_csr(const HBsr& A) {
   HCsr C;
   C.n = A.nbr * A.br;
@@ -543,7 +563,12 @@ struct SellPlan {
   std::vector<int32_t> width;
   std::vector<std::vector<int32_t>> uni;   // empty: explicit slice
 };
-SellPlan sell_plan(const HCsr& C, int B) {
+// node of slot p (lane p % 32 of 32-node group p / 32); -1 past the end
+inline int slot_node(const std::vector<int32_t>& ord, int p, int nn) {
+  if (p >= nn) return -1;
+  return ord.empty() ? p : ord[p];
+}
+SellPlan sell_plan(const HCsr& C, int B, const std::vector<int32_t>& ord) {
   const int nn = C.n / B;
   const int ng = (nn + 31) / 32;
   SellPlan P;
@@ -555,8 +580,8 @@ SellPlan sell_plan(const HCsr& C, int B) {
       const size_t q = (size_t)g * B + c;
       int wmax = 0;
       offs.clear();
-      for (int node = g * 32; node < std::min(nn, g * 32 + 32); ++node) {
-        const int row = node * B + c;
+      for (int p = g * 32; p < std::min(nn, g * 32 + 32); ++p) {
+        const int row = slot_node(ord, p, nn) * B + c;
         wmax = std::max(wmax, C.ptr[row + 1] - C.ptr[row]);
         for (int k = C.ptr[row]; k < C.ptr[row + 1]; ++k) offs.push_back(C.col[k] - row);
       }
@@ -572,21 +597,45 @@ SellPlan sell_plan(const HCsr& C, int B) {
     }
   return P;
 }
+// Nodes sorted by their rows' total length, longest first, within windows
+// of 32 groups (1024 nodes; stable, so equal lengths keep their order).
+std::vector<int32_t> sell_order(const HCsr& C, int B) {
+  const int nn = C.n / B;
+  std::vector<int32_t> ord(nn);
+  std::vector<int32_t> len(nn);
+  for (int i = 0; i < nn; ++i) {
+    ord[i] = i;
+    len[i] = C.ptr[(i + 1) * B] - C.ptr[i * B];
+  }
+  constexpr int W = 32 * 32;
+  for (int w0 = 0; w0 < nn; w0 += W)
+    std::stable_sort(ord.begin() + w0, ord.begin() + std::min(nn, w0 + W),
+                     [&](int a, int b) { return len[a] > len[b]; });
+  return ord;
+}
 }  // namespace
 
-double sell_padding(const HCsr& C, int B) {
+double sell_padding(const HCsr& C, int B, bool sorted) {
   if (B < 1 || C.n % B != 0 || C.col.empty()) return 0.0;
   int64_t slots = 0;
-  for (int32_t w : sell_plan(C, B).width) slots += (int64_t)w * 32;
+  const std::vector<int32_t> ord = sorted ? sell_order(C, B) : std::vector<int32_t>();
+  for (int32_t w : sell_plan(C, B, ord).width) slots += (int64_t)w * 32;
   return (double)slots / (double)C.col.size() - 1.0;
 }
 
-HSell to_sell(const HCsr& C, int B) {
+HSell to_sell(const HCsr& C, int B, bool sorted) {
   if (B < 1 || C.n % B != 0) throw SetupError{"sliced CSR needs whole nodes"};
   HSell S;
   S.n = C.n;
   S.B = B;
-  const SellPlan P = sell_plan(C, B);
+  const int nn = C.n / B;
+  std::vector<int32_t> ord;
+  if (sorted) {
+    ord = sell_order(C, B);
+    S.node = ord;
+    S.node.resize((size_t)((nn + 31) / 32) * 32, -1);
+  }
+  const SellPlan P = sell_plan(C, B, ord);
   S.nslices = (int)P.width.size();
   S.off.assign(S.nslices + 1, 0);
   S.cinfo.assign(S.nslices, 0);
@@ -603,11 +652,10 @@ HSell to_sell(const HCsr& C, int B) {
   S.col.assign(slots, -1);
   S.val.assign(slots, 0.0);
   S.src.assign(slots, -1);
-  const int nn = C.n / B;
-  for (int node = 0; node < nn; ++node)
+  for (int p = 0; p < nn; ++p)
     for (int c = 0; c < B; ++c) {
-      const int row = node * B + c;
-      const int q = (node / 32) * B + c, lane = node % 32;
+      const int row = slot_node(ord, p, nn) * B + c;
+      const int q = (p / 32) * B + c, lane = p % 32;
       const std::vector<int32_t>& u = P.uni[q];
       size_t kk = 0;   // position in the union (uniform slices)
       for (int k = C.ptr[row]; k < C.ptr[row + 1]; ++k) {
@@ -621,6 +669,82 @@ HSell to_sell(const HCsr& C, int B) {
         S.col[e] = C.col[k];
         S.val[e] = C.val[k];
         S.src[e] = k;
+      }
+    }
+  return S;
+}
+
+namespace {
+// Slot order of to_bsell: rows sorted by length, longest first, within
+// windows of window * R rows (stable, so equal lengths keep row order).
+std::vector<int32_t> bsell_order(const HBsr& A, int R, int window) {
+  std::vector<int32_t> ord(A.nbr);
+  for (int i = 0; i < A.nbr; ++i) ord[i] = i;
+  const int W = std::max(1, window) * R;
+  for (int w0 = 0; w0 < A.nbr; w0 += W) {
+    const int w1 = std::min(A.nbr, w0 + W);
+    std::stable_sort(ord.begin() + w0, ord.begin() + w1, [&](int a, int b) {
+      return A.ptr[a + 1] - A.ptr[a] > A.ptr[b + 1] - A.ptr[b];
+    });
+  }
+  return ord;
+}
+}  // namespace
+
+double bsell_padding(const HBsr& A, int window) {
+  if (A.br != A.bc || A.nnzb() == 0) return 0.0;
+  const int R = 32 / A.br;
+  const std::vector<int32_t> ord = bsell_order(A, R, window);
+  int64_t slots = 0;
+  for (int q0 = 0; q0 < A.nbr; q0 += R) {
+    int w = 0;
+    for (int i = q0; i < std::min(A.nbr, q0 + R); ++i)
+      w = std::max(w, A.ptr[ord[i] + 1] - A.ptr[ord[i]]);
+    slots += (int64_t)w * R;
+  }
+  return (double)slots / (double)A.nnzb() - 1.0;
+}
+
+HBSell to_bsell(const HBsr& A, int window) {
+  if (A.br != A.bc || A.br < 1 || A.br > 4) throw SetupError{"block slices need square blocks"};
+  HBSell S;
+  S.nbr = A.nbr;
+  S.B = A.br;
+  S.R = 32 / A.br;
+  const int R = S.R, bs = A.bsz();
+  const std::vector<int32_t> ord = bsell_order(A, R, window);
+  S.nslices = (A.nbr + R - 1) / R;
+  S.perm.assign((size_t)S.nslices * R, -1);
+  S.off.assign(S.nslices + 1, 0);
+  for (int q = 0; q < S.nslices; ++q) {
+    int w = 0;
+    for (int i = 0; i < R && q * R + i < A.nbr; ++i) {
+      const int row = ord[q * R + i];
+      S.perm[(size_t)q * R + i] = row;
+      w = std::max(w, A.ptr[row + 1] - A.ptr[row]);
+    }
+    if ((int64_t)S.off[q] + w > INT32_MAX / (32 * 16)) throw SetupError{"block slices too large"};
+    S.off[q + 1] = S.off[q] + w;
+  }
+  const size_t nb = (size_t)S.off[S.nslices] * R;
+  S.col.assign(nb, 0);
+  S.val.assign(nb * bs, 0.0);
+  for (int q = 0; q < S.nslices; ++q)
+    for (int i = 0; i < R; ++i) {
+      const int row = S.perm[(size_t)q * R + i];
+      const int w = S.off[q + 1] - S.off[q];
+      for (int k = 0; k < w; ++k) {
+        const size_t e = ((size_t)S.off[q] + k) * R + i;
+        if (row < 0) continue;
+        const int len = A.ptr[row + 1] - A.ptr[row];
+        if (k < len) {
+          const int src = A.ptr[row] + k;
+          S.col[e] = A.col[src];
+          std::copy(A.val.begin() + (size_t)src * bs, A.val.begin() + (size_t)(src + 1) * bs,
+                    S.val.begin() + e * bs);
+        } else {
+          S.col[e] = row;   // zero block on the row's own column
+        }
       }
     }
   return S;

@@ -78,6 +78,11 @@ std::vector<int32_t> aggregate(const HBsr& A, double eps, int* n_agg);
 std::vector<double> spai0(const HBsr& A);
 std::vector<double> jacobi(const HBsr& A, double omega);
 
+// A M for a block-diagonal M (n_brows * B * B blocks): block (i, j) of the
+// result is A_ij M_j, on A's pattern.  With x = M f, the residual f - A x of
+// a zero-guess smoothing step is f - (A M) f, one product with f.
+HBsr scale_columns(const HBsr& A, const std::vector<double>& M);
+
 // Scalar CSR of the nonzero entries of a block matrix (columns sorted per
 // row); fill = nonzeros / stored block values.
 HCsr to_scalar_csr(const HBsr& A);
@@ -119,10 +124,38 @@ struct HSell {
   std::vector<int32_t> cinfo; // per slice: 0 explicit, -1 - (first uoff index) uniform
   std::vector<int32_t> uoff;  // uniform slices: column offset of each slice column
   std::vector<uint32_t> umask;
+  // Sorted form (irregular operators): the node of lane i of group g is
+  // node[g * 32 + i] (-1: none) instead of g * 32 + i -- nodes sorted by
+  // their rows' total length within windows of 1024 nodes, so that a
+  // slice's rows have nearly equal lengths.  Empty: natural order.
+  std::vector<int32_t> node;
 };
-// Stored entries / nonzeros - 1 of the sliced form (B must divide C.n).
-double sell_padding(const HCsr& C, int B);
-HSell to_sell(const HCsr& C, int B);
+// Stored entries / nonzeros - 1 of the sliced form (B must divide C.n),
+// in natural or sorted node order.
+double sell_padding(const HCsr& C, int B, bool sorted = false);
+HSell to_sell(const HCsr& C, int B, bool sorted = false);
+
+// Block-row slices of a square block matrix (the FP64 block levels): the
+// block rows are sorted by length (longest first, stable) within windows
+// of `window` slices, and each run of R = 32 / B consecutive sorted rows
+// forms a slice that one warp owns with one lane per scalar row -- no lane
+// shares a row, so no cross-lane sums, and the rows of a slice have
+// nearly equal lengths, so few lanes idle.  Each slice is padded to its
+// longest row.  Entry k of slot i of slice q is block e = (off[q] + k) * R
+// + i: column col[e], values val[e * B * B ...] row-major, so a warp's
+// loads of entry k read R consecutive blocks.  Padding entries repeat the
+// slot's own block row as column with zero values; empty slots (the last
+// slice) have perm -1.
+struct HBSell {
+  int nbr = 0, B = 1, R = 8, nslices = 0;
+  std::vector<int32_t> perm;   // nslices * R: block row of each slot, -1 if none
+  std::vector<int32_t> off;    // nslices + 1, in entries of R blocks
+  std::vector<int32_t> col;    // off[nslices] * R
+  std::vector<double> val;     // off[nslices] * R * B * B
+};
+HBSell to_bsell(const HBsr& A, int window);
+// Stored blocks / stored blocks of A - 1 of that layout.
+double bsell_padding(const HBsr& A, int window);
 
 // Schur split of node blocks (nvel+1)^2 into A (nvel^2), G (nvel x 1),
 // D (1 x nvel), C (1x1) on K's block pattern, and S_hat of Eq. SchurApprox.

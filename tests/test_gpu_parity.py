@@ -102,13 +102,21 @@ def _import(Ho, B, **kw):
     return gb.import_hierarchy(As, Ps, Rs, Ms, Ho.Ainv_coarse, B, gb.params_default(**kw))
 
 
-@pytest.mark.parametrize("fmt", ["0", "1", "2", "3"])
+@pytest.mark.parametrize("fmt", ["0", "0u", "1", "2", "3", "1b", "3o"])
 @pytest.mark.parametrize("cfg", [("c2", 9, "jacobi"), ("c2", 10, "spai0"), ("c1", 9, "spai0")])
 def test_vcycle_on_imported_oracle_hierarchy(cfg, fmt, monkeypatch):
     """Level formats: 0 automatic (scalar CSR where blocks are mostly zero,
     sliced where that pads little), 1 block CSR everywhere, 2 plain scalar
-    CSR wherever possible, 3 sliced scalar CSR wherever possible."""
-    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
+    CSR wherever possible, 3 sliced scalar CSR wherever possible; 1b block
+    form everywhere with every block level's residual and relaxation in
+    block-row slices (the transposed cycle keeps the block CSR form); 3o
+    slices with the nodes of every irregular operator sorted by length.
+    Every FP64 level in slices fuses its zero-guess pre-smoothing step
+    with the residual (r = f - (A M) f); 0u keeps the two passes."""
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt[0])
+    monkeypatch.setenv("GBS_FUSE", "0" if fmt.endswith("u") else "1")
+    monkeypatch.setenv("GBS_BSELL", "1" if fmt.endswith("b") else "0")
+    monkeypatch.setenv("GBS_SELL_SORT", "1" if fmt.endswith("o") else "0")
     name, N, relax = cfg
     s = si.make_system(name, N=N)
     B = s.bdim
@@ -133,6 +141,7 @@ def test_vcycle_every_lane_group_width(name, G, S, monkeypatch):
     256-thread CTA per block row -- and compare with the oracle."""
     monkeypatch.setenv("GBS_SPMV_GROUP", G)
     monkeypatch.setenv("GBS_SPMV_SPLIT", S)
+    monkeypatch.setenv("GBS_BSELL", "0")
     s = si.make_system(name, N=9)
     B = s.bdim
     A = bsr.from_arrays(s.indptr, s.indices, s.data, B)
@@ -236,7 +245,7 @@ def _import_schur(s, pc, **kw):
                            pc.M_S.reshape(-1) if pc.M_S is not None else None, p)
 
 
-@pytest.mark.parametrize("fmt", ["0", "1", "2", "3"])
+@pytest.mark.parametrize("fmt", ["0", "1", "2", "3", "3o"])
 @pytest.mark.parametrize("variant", [("full", "amg"), ("lower", "amg"), ("full", "spai0"),
                                      ("lower", "jacobi")])
 def test_schur_apply_on_imported_oracle_hierarchy(variant, fmt, monkeypatch):
@@ -244,8 +253,9 @@ def test_schur_apply_on_imported_oracle_hierarchy(variant, fmt, monkeypatch):
     hierarchies: the gather, the coupling kernels (r_p - D u, r_u - G p and
     their transposes through the transpose map), the inner V-cycles and
     the scatter match the oracle to 1e-12, forward and transposed, in every
-    level format."""
-    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
+    level format (3o: slices with sorted nodes wherever rows are irregular)."""
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt[0])
+    monkeypatch.setenv("GBS_SELL_SORT", "1" if fmt.endswith("o") else "0")
     order, pressure = variant
     s = si.make_system("c3", N=9)
     K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
@@ -278,7 +288,7 @@ def test_schur_import_rejects_mismatched_levels():
 FMT = {gb.GBS_FP32: "fp32", gb.GBS_BF16: "bf16"}
 
 
-@pytest.mark.parametrize("fmt", ["0", "1", "2", "3"])
+@pytest.mark.parametrize("fmt", ["0", "1", "2", "3", "3s", "3d", "1b", "3o"])
 @pytest.mark.parametrize("precision", [gb.GBS_FP32, gb.GBS_BF16])
 def test_mixed_vcycle_matches_oracle_on_cast_hierarchy(precision, fmt, monkeypatch):
     """Mixed forms (Section 4, Listing V4; BF16 storage with FP32
@@ -289,8 +299,14 @@ def test_mixed_vcycle_matches_oracle_on_cast_hierarchy(precision, fmt, monkeypat
     vector storage: a few units of 2^-24 per operation over the levels, so
     1e-5 relative in the max norm for both forms.  Formats 2 and 3 put
     every level in scalar CSR and in slices (the staged bulk-copy
-    kernels)."""
-    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
+    kernels, or the direct ones where every slice is uniform); 3s / 3d
+    send every sliced operator to the staged / direct kernels; 1b forces
+    block-row slices on every block level."""
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt[0])
+    monkeypatch.setenv("GBS_BSELL", "1" if fmt.endswith("b") else "0")
+    monkeypatch.setenv("GBS_SELL_SORT", "1" if fmt.endswith("o") else "0")
+    if fmt[1:] in ("s", "d"):
+        monkeypatch.setenv("GBS_SELL_DIRECT", "0" if fmt.endswith("s") else "1")
     s = si.make_system("c2", N=10)
     A = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
     Ho = amg.build_hierarchy(A, amg.AmgParams(coarse_enough=60, relax="jacobi"))
@@ -884,4 +900,25 @@ def test_schur_ilut_pressure_amg_matches_oracle():
         z = host(gb.apply_precond(H, dev(r), transpose=tr))
         assert rel_inf(z, pc.apply(r, transpose=tr)) <= 1e-10, tr
     x, info = gb.solve(H, dev(s.b))
+    assert info.converged and _true_rel(s, host(x)) <= 1e-8
+
+
+def test_pipeline_wait_timeout_is_reported(monkeypatch):
+    """The staged FP32 kernels (every level in slices, bulk copies on an
+    mbarrier) with each pipeline wait bounded at 2^0 SM clocks: the first
+    wait gives up before its copy lands, the warp records the timeout in
+    the solve's scalar block after waiting (full bound) for every copy it
+    has in flight, and the solve returns GBS_ERR_CUDA.  Nothing hangs and
+    nothing faults; a fresh handle with the default bound then solves."""
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", "3")
+    monkeypatch.setenv("GBS_SELL_DIRECT", "0")
+    s = si.make_system("c2", N=10)
+    H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
+                           _params(s, relax=gb.GBS_JACOBI, precision=gb.GBS_FP32, wait_log2=0))
+    with pytest.raises(gb.GbsError) as e:
+        gb.solve(H, dev(s.b))
+    assert e.value.status == -2 and "timed out" in str(e.value)
+    H2 = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
+                            _params(s, relax=gb.GBS_JACOBI, precision=gb.GBS_FP32))
+    x, info = gb.solve(H2, dev(s.b))
     assert info.converged and _true_rel(s, host(x)) <= 1e-8
