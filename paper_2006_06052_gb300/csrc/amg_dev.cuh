@@ -237,10 +237,31 @@ inline bool sell_direct(const DevSell<VT>& A) {
   if (const char* e = std::getenv("GBS_SELL_DIRECT")) return e[0] == '1';
   return false;
 }
+// One warp per 32-node group (B slices, contiguous stores) unless
+// GBS_SELL_GROUP=0 asks for one warp per slice (measurement and tests).
+inline bool sell_grouped() {
+  const char* e = std::getenv("GBS_SELL_GROUP");
+  return !(e && e[0] == '0');
+}
+template <int B, int MODE, class VT, class XT, class YT, class AT>
+void sell_spmv_g(const DevSell<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
+  const int64_t groups = (int64_t)A.nslices / B;
+  if (sell_direct<VT, AT>(A))
+    k_sell_spmv_direct_g<B, MODE, VT, XT, YT, AT><<<grid_for(groups * 32), 256, 0, s>>>(A, x, f, y);
+  else
+    launch_sell(k_sell_spmv_g<B, MODE, VT, XT, YT, AT>, sell_smem_bytes<VT>(),
+                (groups + SELL_WARPS - 1) / SELL_WARPS, s, A, x, f, y);
+}
 template <int MODE, class VT, class XT, class YT, class AT>
 void sell_spmv(const DevSell<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
   if (A.n == 0) return;
-  if (sell_direct<VT, AT>(A)) {
+  if (A.B > 1 && sell_grouped()) {
+    switch (A.B) {
+      case 2: sell_spmv_g<2, MODE, VT, XT, YT, AT>(A, x, f, y, s); break;
+      case 3: sell_spmv_g<3, MODE, VT, XT, YT, AT>(A, x, f, y, s); break;
+      default: sell_spmv_g<4, MODE, VT, XT, YT, AT>(A, x, f, y, s); break;
+    }
+  } else if (sell_direct<VT, AT>(A)) {
     k_sell_spmv_direct<MODE, VT, XT, YT, AT>
         <<<grid_for((int64_t)A.nslices * 32), 256, 0, s>>>(A, x, f, y);
   } else {

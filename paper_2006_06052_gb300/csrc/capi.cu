@@ -324,12 +324,17 @@ void outer(const Handle& h, bool tr, int mode, const double* x, const double* f,
            const double* w0, int self_dot, int slot, int op, bool reduce, cudaStream_t s) {
   NvtxRange range(mode == SPMV_RESID ? "outer residual" : "outer SpMV");
   if (!tr && h.k_csr && h.k_sell) {
-    if (mode == SPMV_RESID)
-      launch_resident(k_outer_sell<SPMV_RESID>, h.red.cap, s, h.Ks, x, f, y, w0, self_dot, h.red,
-                      slot, op, (int)reduce);
-    else
-      launch_resident(k_outer_sell<SPMV_SET>, h.red.cap, s, h.Ks, x, f, y, w0, self_dot, h.red,
-                      slot, op, (int)reduce);
+#define GBS_OSELL(MM, BB)                                                                      \
+  launch_resident(k_outer_sell<MM, BB>, h.red.cap, s, h.Ks, x, f, y, w0, self_dot, h.red, slot, \
+                  op, (int)reduce)
+    const bool res = mode == SPMV_RESID;
+    switch (h.B) {
+      case 1: if (res) GBS_OSELL(SPMV_RESID, 1); else GBS_OSELL(SPMV_SET, 1); break;
+      case 2: if (res) GBS_OSELL(SPMV_RESID, 2); else GBS_OSELL(SPMV_SET, 2); break;
+      case 3: if (res) GBS_OSELL(SPMV_RESID, 3); else GBS_OSELL(SPMV_SET, 3); break;
+      default: if (res) GBS_OSELL(SPMV_RESID, 4); else GBS_OSELL(SPMV_SET, 4); break;
+    }
+#undef GBS_OSELL
     GBS_LAUNCH_CHECK();
     return;
   }

@@ -241,10 +241,12 @@ __global__ void __launch_bounds__(RED_THREADS, 4)
 }
 
 // y = K x (RESID: y = f - K x) with K in 32-node component slices, one
-// warp per slice (grid-stride), direct loads (sell.cuh); dots as k_outer.
-// On a stencil operator every slice is uniform: no column loads, and the
-// gather address comes from the row index.
-template <int MODE>
+// warp per 32-node group (grid-stride), direct loads (sell.cuh); dots as
+// k_outer.  The warp walks the group's B slices and each lane then stores
+// its node's B rows contiguously.  On a stencil operator every slice is
+// uniform: no column loads, and the gather address comes from the row
+// index.
+template <int MODE, int B>
 __global__ void __launch_bounds__(RED_THREADS, 4)
     k_outer_sell(DevSell<double> K, const double* __restrict__ x, const double* __restrict__ f,
                  double* __restrict__ y, const double* __restrict__ w0, int self_dot, Red R,
@@ -252,16 +254,24 @@ __global__ void __launch_bounds__(RED_THREADS, 4)
   double d[2] = {0.0, 0.0};
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < K.nslices; q += nw) {
-    const int64_t g = q / K.B;
+  const int64_t ng = K.nslices / B;
+  for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < ng; g += nw) {
     const int64_t node = sell_node(K, g, lane);
-    const int64_t row = (node < 0 ? 0 : node) * K.B + (q - g * K.B);
-    const double acc = sell_row_dot_direct<double, double, double>(K, x, (int)q, lane, row);
+    const int64_t nd = node < 0 ? 0 : node;   // no entries in an empty lane
+    double res[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c)
+      res[c] = sell_row_dot_direct<double, double, double>(K, x, (int)(g * B + c), lane, nd * B + c);
     if (node >= 0) {
-      const double val = MODE == SPMV_RESID ? f[row] - acc : acc;
-      y[row] = val;
-      if (w0) d[0] += val * w0[row];
-      if (self_dot) d[1] += val * val;
+      double fv[B];
+      if (MODE == SPMV_RESID) load_run<B, double, double, false>(f + node * B, fv);
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        const double val = MODE == SPMV_RESID ? fv[c] - res[c] : res[c];
+        y[node * B + c] = val;
+        if (w0) d[0] += val * w0[node * B + c];
+        if (self_dot) d[1] += val * val;
+      }
     }
   }
   if (reduce) grid_reduce<2>(d, R, slot, op);

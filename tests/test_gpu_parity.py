@@ -102,7 +102,7 @@ def _import(Ho, B, **kw):
     return gb.import_hierarchy(As, Ps, Rs, Ms, Ho.Ainv_coarse, B, gb.params_default(**kw))
 
 
-@pytest.mark.parametrize("fmt", ["0", "0u", "1", "2", "3", "1b", "3o"])
+@pytest.mark.parametrize("fmt", ["0", "0u", "1", "2", "3", "3w", "1b", "3o"])
 @pytest.mark.parametrize("cfg", [("c2", 9, "jacobi"), ("c2", 10, "spai0"), ("c1", 9, "spai0")])
 def test_vcycle_on_imported_oracle_hierarchy(cfg, fmt, monkeypatch):
     """Level formats: 0 automatic (scalar CSR where blocks are mostly zero,
@@ -112,9 +112,11 @@ def test_vcycle_on_imported_oracle_hierarchy(cfg, fmt, monkeypatch):
     block-row slices (the transposed cycle keeps the block CSR form); 3o
     slices with the nodes of every irregular operator sorted by length.
     Every FP64 level in slices fuses its zero-guess pre-smoothing step
-    with the residual (r = f - (A M) f); 0u keeps the two passes."""
+    with the residual (r = f - (A M) f); 0u keeps the two passes.  Sliced
+    products run one warp per 32-node group; 3w runs one warp per slice."""
     monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt[0])
     monkeypatch.setenv("GBS_FUSE", "0" if fmt.endswith("u") else "1")
+    monkeypatch.setenv("GBS_SELL_GROUP", "0" if fmt.endswith("w") else "1")
     monkeypatch.setenv("GBS_BSELL", "1" if fmt.endswith("b") else "0")
     monkeypatch.setenv("GBS_SELL_SORT", "1" if fmt.endswith("o") else "0")
     name, N, relax = cfg
@@ -288,7 +290,7 @@ def test_schur_import_rejects_mismatched_levels():
 FMT = {gb.GBS_FP32: "fp32", gb.GBS_BF16: "bf16"}
 
 
-@pytest.mark.parametrize("fmt", ["0", "1", "2", "3", "3s", "3d", "1b", "3o"])
+@pytest.mark.parametrize("fmt", ["0", "1", "2", "3", "3s", "3d", "3w", "1b", "3o"])
 @pytest.mark.parametrize("precision", [gb.GBS_FP32, gb.GBS_BF16])
 def test_mixed_vcycle_matches_oracle_on_cast_hierarchy(precision, fmt, monkeypatch):
     """Mixed forms (Section 4, Listing V4; BF16 storage with FP32
@@ -305,6 +307,7 @@ def test_mixed_vcycle_matches_oracle_on_cast_hierarchy(precision, fmt, monkeypat
     monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt[0])
     monkeypatch.setenv("GBS_BSELL", "1" if fmt.endswith("b") else "0")
     monkeypatch.setenv("GBS_SELL_SORT", "1" if fmt.endswith("o") else "0")
+    monkeypatch.setenv("GBS_SELL_GROUP", "0" if fmt.endswith("w") else "1")
     if fmt[1:] in ("s", "d"):
         monkeypatch.setenv("GBS_SELL_DIRECT", "0" if fmt.endswith("s") else "1")
     s = si.make_system("c2", N=10)
@@ -909,14 +912,22 @@ def test_pipeline_wait_timeout_is_reported(monkeypatch):
     wait gives up before its copy lands, the warp records the timeout in
     the solve's scalar block after waiting (full bound) for every copy it
     has in flight, and the solve returns GBS_ERR_CUDA.  Nothing hangs and
-    nothing faults; a fresh handle with the default bound then solves."""
+    nothing faults; a fresh handle with the default bound then solves.
+    A wait that finds its copy already landed succeeds whatever the bound,
+    so L2 is flushed first: the first copies then come from DRAM and take
+    far longer than the wait allows."""
     monkeypatch.setenv("GBS_LEVEL_FORMAT", "3")
     monkeypatch.setenv("GBS_SELL_DIRECT", "0")
     s = si.make_system("c2", N=10)
     H = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
                            _params(s, relax=gb.GBS_JACOBI, precision=gb.GBS_FP32, wait_log2=0))
+    b = dev(s.b)
+    flush = torch.zeros(32 << 20, dtype=torch.float64, device="cuda")   # 256 MB > L2
+    flush += 1.0
+    torch.cuda.synchronize()
+    del flush
     with pytest.raises(gb.GbsError) as e:
-        gb.solve(H, dev(s.b))
+        gb.solve(H, b)
     assert e.value.status == -2 and "timed out" in str(e.value)
     H2 = gb.build_hierarchy(s.indptr, s.indices, s.data, 4,
                             _params(s, relax=gb.GBS_JACOBI, precision=gb.GBS_FP32))
