@@ -137,8 +137,11 @@ def level1_relax_roofline(gb, H, B, precision, timed, peak, peak_kind, fp64):
     flops = 2.0 * (nnzb * B * B if block else nnz) + 2.0 * n * B + n
     gbs = nbytes / (ms * 1e-3) / 1e9
     tflops = flops / (ms * 1e-3) / 1e12
-    kname = ("k_relax" if block else "k_csr_relax") + (" (FP64, %dx%d blocks)" % (B, B) if block
-                                                     else " (scalar CSR)")
+    layout, _ = gb.level_format(H, 0, 1)
+    kname = {"block slices": "k_bsell_relax (%dx%d blocks in block-row slices)" % (B, B),
+             "block": "k_relax (%dx%d blocks)" % (B, B),
+             "csr": "k_csr_relax (scalar CSR)",
+             "sliced": "k_sell_relax (scalar slices)"}[layout]
     desc = ("%s: level-1 relaxation sweep y = x + M (f - A_1 x), %d block rows, %d stored blocks"
             % (kname, nbr, nnzb))
     traffic = profiled_traffic("k_relax_level1", "c2") if precision == 0 else None
@@ -368,11 +371,14 @@ def time_cpu_oracle(system, wl, iters_to_scale, sample_iters=3, calibrate=False)
         def run(maxiter):
             return krylov.gmres(lambda v: Ks @ v, pc.apply, s.b, m=30, tol=1e-8, maxiter=maxiter)
     full_iters = None
+    full_s = None
     if calibrate:
+        t0 = time.perf_counter()
         _, info = run(10000)
+        full_s = time.perf_counter() - t0
         full_iters = info.iters
         iters_to_scale = full_iters
-    return run, iters_to_scale, full_iters, sample_iters
+    return run, iters_to_scale, full_iters, sample_iters, full_s
 
 
 def cpu_oracle_sample(run, sample_iters):
@@ -417,8 +423,8 @@ def run_reference(args, world, rank):
     import stokes_inputs as si
     wl = args.workload
     s = si.make_system(WORKLOADS[wl]["system"])
-    run, iters, full_iters, k = time_cpu_oracle(s, wl, None, sample_iters=args.sample_iters,
-                                                calibrate=True)
+    run, iters, full_iters, k, full_s = time_cpu_oracle(s, wl, None, sample_iters=args.sample_iters,
+                                                        calibrate=True)
     for _ in range(args.warmup):
         cpu_oracle_sample(run, 1)
     per = []
@@ -427,7 +433,9 @@ def run_reference(args, world, rank):
     per_it = float(np.mean(per))
     value = per_it * full_iters * 1e3
     sample = ("oracle setup untimed; per step %d Krylov iterations of the full-size workload "
-              "timed, scaled by the oracle's own iteration count (%d) to one solve" % (k, full_iters))
+              "timed, scaled by the oracle's own iteration count (%d) to one solve; one "
+              "complete oracle solve, timed once as a check of that scaling, took %.1f s"
+              % (k, full_iters, full_s))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -435,7 +443,7 @@ def run_reference(args, world, rank):
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-           "iterations": full_iters}
+           "iterations": full_iters, "full_solve_ms": full_s * 1e3}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -677,7 +685,7 @@ def main():
         "hierarchy_bytes": gb.hierarchy_info(H)["bytes"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        run, it_scale, _, k = time_cpu_oracle(s, wl, iters[-1], sample_iters=args.sample_iters)
+        run, it_scale, _, k, _ = time_cpu_oracle(s, wl, iters[-1], sample_iters=args.sample_iters)
         per_it = cpu_oracle_sample(run, k)
         out["cpu_baseline"] = {
             "value": per_it * it_scale * 1e3, "unit": UNIT, "cores": 1, "kind": "oracle",

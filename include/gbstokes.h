@@ -234,6 +234,16 @@ gbs_status gbs_precond_bytes(const gbs_hierarchy* h, double* bytes_per_apply);
  * the next solve or spmv. */
 gbs_status gbs_outer_format(const gbs_hierarchy* h, int32_t* format, int64_t* stored);
 
+/* Layout in which level `level` (below the coarsest) of AMG `which` (0
+ * monolithic / velocity, 1 pressure) runs its forward products (no
+ * counterpart in the paper; the library's per-level format choice, for
+ * measurement): *format = 0 block CSR, 1 scalar CSR of the nonzeros, 2
+ * those nonzeros in 32-node component slices, 3 block-row slices; plus 4
+ * when the level fuses its zero-guess smoothing step with the residual
+ * (x = M f, r = f - (A M) f in one pass).  Host only. */
+gbs_status gbs_level_format(const gbs_hierarchy* h, int32_t which, int32_t level,
+                            int32_t* format);
+
 /* One operation on level `level` (below the coarsest) of AMG `which` (0
  * monolithic / velocity, 1 pressure), launched exactly as the V-cycle
  * launches it (no counterpart in the paper; for measurement and tests):

@@ -41,6 +41,7 @@ EXPORTED = [
     "gbs_hierarchy_info", "gbs_export_level", "gbs_import_hierarchy", "gbs_destroy",
     "gbs_last_error", "gbs_kernel_launches", "gbs_spmv_dots_noalloc", "gbs_precond_bytes",
     "gbs_outer_format", "gbs_level_apply", "gbs_import_schur", "gbs_fp64_peak",
+    "gbs_level_format",
 ]
 
 
@@ -136,6 +137,7 @@ def load_library():
         "gbs_import_schur": [c.POINTER(_Bsr), c.POINTER(_Levels), c.POINTER(_Levels), P,
                              c.POINTER(Params), P, c.POINTER(P)],
         "gbs_fp64_peak": [c.POINTER(c.c_double), c.POINTER(c.c_int32), P, P],
+        "gbs_level_format": [P, c.c_int32, c.c_int32, c.POINTER(c.c_int32)],
         "gbs_destroy": [P],
         "gbs_precond_bytes": [P, c.POINTER(c.c_double)],
         "gbs_outer_format": [P, c.POINTER(c.c_int32), c.POINTER(c.c_int64)],
@@ -444,6 +446,18 @@ def fp64_peak(stream=None):
     _check(load_library().gbs_fp64_peak(ctypes.byref(t), ctypes.byref(n),
                                         ctypes.c_void_p(sink.data_ptr()), _stream_ptr(stream)))
     return t.value, n.value
+
+
+LEVEL_LAYOUTS = ("block", "csr", "sliced", "block slices")
+
+
+def level_format(H: Hierarchy, which: int, level: int):
+    """(layout name, fused) of level `level` of AMG `which`: the layout its
+    forward products run in, and whether its zero-guess smoothing step is
+    fused with the residual."""
+    f = ctypes.c_int32()
+    _check(load_library().gbs_level_format(H.handle, which, level, ctypes.byref(f)))
+    return LEVEL_LAYOUTS[f.value & 3], bool(f.value & 4)
 
 
 OUTER_FORMATS = ("block", "csr", "sliced")

@@ -116,6 +116,16 @@ DevCsr<VT> upload_csr(Arena& ar, const HCsr& C, cudaStream_t s, std::vector<std:
     int sp = std::atoi(e);
     if (sp == 1 || sp == 2 || sp == 4 || sp == 8) d.S = sp;
   }
+  // FP32/BF16 values (not FP64-pipe bound): long rows stream as aligned
+  // 16-byte chunks over G lanes (group_row_fwd with B = 1), so a warp's
+  // loads cover contiguous runs instead of S lanes striding one entry at a
+  // time.  GBS_CSR_CHUNK=0 keeps the strided lanes (measurement, tests).
+  if (sizeof(VT) < 8 && C.n > 0) {
+    const double chunks = (double)C.col.size() / C.n * sizeof(VT) / 16.0;
+    d.G = chunks >= 48 ? 32 : chunks >= 16 ? 16 : chunks >= 4 ? 8 : 0;
+    if (const char* e = std::getenv("GBS_CSR_CHUNK"))
+      if (e[0] == '0') d.G = 0;
+  }
   return d;
 }
 
@@ -296,9 +306,23 @@ void sell_relax(int B, const DevSell<VT>& A, const VT* M, const XT* f, const XT*
   GBS_LAUNCH_CHECK();
 }
 
+template <int B, bool TR, int MODE, class VT, class XT, class YT, class AT>
+void spmv_B(const DevBsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s);
+
 template <int MODE, class VT, class XT, class YT, class AT>
 void csr_spmv(const DevCsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
   if (A.n == 0) return;
+  if (A.G) {   // a scalar CSR matrix is a block CSR matrix with 1 x 1 blocks
+    DevBsr<VT> v;
+    v.nbr = v.nbc = A.n;
+    v.rp = A.rp;
+    v.col = A.col;
+    v.val = A.val;
+    v.G = A.G;
+    spmv_B<1, false, MODE, VT, XT, YT, AT>(v, x, f, y, s);
+    GBS_LAUNCH_CHECK();
+    return;
+  }
   switch (A.S) {
     case 2: k_csr_spmv<2, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<1, 2>(A.n)), 256, 0, s>>>(A, x, f, y); break;
     case 4: k_csr_spmv<4, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<1, 4>(A.n)), 256, 0, s>>>(A, x, f, y); break;
@@ -615,6 +639,11 @@ struct DevAmg {
   }
 
   int64_t n0() const { return lev[0].n; }
+  int layout(size_t l) const {
+    const Lev& L = lev[l];
+    const int base = L.a_bsell ? 3 : L.a_sell ? 2 : L.a_csr ? 1 : 0;
+    return base + (L.fused ? 4 : 0);
+  }
 
   // z = S r with S the approximate (LU)^-1 of an ILUT level (S^T when TR):
   // ilu_sweeps Jacobi sweeps per triangular solve.  Returns the buffer
@@ -877,6 +906,7 @@ struct AmgPrecond final : DevPrecond {
                  static_cast<ST*>(y), s);
   }
   int vector_bytes() const override { return (int)sizeof(ST); }
+  int level_layout(int, int l) const override { return amg.layout((size_t)l); }
   int nlevels(int which) const override { return which == 0 ? (int)amg.lev.size() : 0; }
   int64_t level_rows(int, int l) const override { return amg.lev[l].n / amg.B; }
   int64_t level_nnzb(int, int l) const override { return amg.lev[l].nnzb_A; }
@@ -1069,6 +1099,9 @@ struct SchurPrecond final : DevPrecond {
                static_cast<ST*>(y), s);
   }
   int vector_bytes() const override { return (int)sizeof(ST); }
+  int level_layout(int which, int l) const override {
+    return which == 0 ? A.layout((size_t)l) : S.layout((size_t)l);
+  }
   int nlevels(int which) const override {
     return which == 0 ? (int)A.lev.size() : (int)S.lev.size();
   }

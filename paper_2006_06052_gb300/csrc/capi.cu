@@ -1243,6 +1243,20 @@ gbs_status gbs_level_apply(gbs_hierarchy* hh, int32_t which, int32_t level, int3
   });
 }
 
+gbs_status gbs_level_format(const gbs_hierarchy* hh, int32_t which, int32_t level,
+                            int32_t* format) {
+  return guarded([&]() -> gbs_status {
+    if (!hh || !format) throw SetupError{"null argument"};
+    const Handle& h = hh->h;
+    need_device(h);
+    if (which < 0 || which > 1 || (which == 1 && !h.schur)) throw SetupError{"bad hierarchy id"};
+    if (level < 0 || level + 1 >= h.pc->nlevels(which))
+      throw SetupError{"level must be below the coarsest"};
+    *format = h.pc->level_layout(which, level);
+    return GBS_OK;
+  });
+}
+
 gbs_status gbs_outer_format(const gbs_hierarchy* hh, int32_t* format, int64_t* stored) {
   return guarded([&]() -> gbs_status {
     if (!hh || !format || !stored) throw SetupError{"null argument"};

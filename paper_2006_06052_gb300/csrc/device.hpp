@@ -87,6 +87,10 @@ struct DevPrecond {
     throw SetupError{"level_op is not available for this preconditioner"};
   }
   virtual int vector_bytes() const { return 8; }
+  // layout A_l of AMG `which` runs in (forward): 0 block CSR, 1 scalar CSR,
+  // 2 scalar slices, 3 block-row slices; +4 when the level fuses its
+  // zero-guess smoothing step with the residual
+  virtual int level_layout(int which, int l) const { return 0; }
 };
 
 struct PrecondOptions {

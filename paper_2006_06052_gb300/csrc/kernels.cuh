@@ -46,6 +46,7 @@ struct DevCsr {
   const int* col = nullptr;
   const VT* val = nullptr;
   int S = 1;
+  int G = 0;   // FP32/BF16 products: G lanes a row stream 16-byte chunks (0: S lanes a row)
 };
 
 // Sliced scalar CSR (see HSell and sell.cuh): slice q holds component
@@ -882,19 +883,23 @@ __global__ void __launch_bounds__(256, 4) k_cast_mapply(int nbr, const VT* __res
                                                      const double* __restrict__ r,
                                                      XT* __restrict__ fin, XT* __restrict__ x) {
   RowMap<B> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
-  if (!m.lane_ok || m.brow >= nbr) return;
-  double rv[B];
-  load_run<B, double, double, false>(r + (size_t)m.brow * B, rv);
+  if ((int64_t)(blockIdx.x * (int64_t)blockDim.x + threadIdx.x - (threadIdx.x & 31)) / 32 *
+          RowMap<B>::RPW >= nbr)
+    return;   // the whole warp is past the last row
+  const bool ok = m.lane_ok && m.brow < nbr;
+  const size_t o = (size_t)m.brow * B + m.r;
+  // each lane reads its own entry; the node's B entries meet by shuffles
+  const XT ri = ok ? (XT)r[o] : XT(0);
   AT fv[B], mr[B];
 #pragma unroll
-  for (int c = 0; c < B; ++c) fv[c] = cvt<AT>((XT)rv[c]);
+  for (int c = 0; c < B; ++c) fv[c] = cvt<AT>(__shfl_sync(0xffffffffu, ri, (m.base + c) & 31));
+  if (!ok) return;
   if constexpr (!TR) load_run<B, VT, AT, false>(M + (size_t)m.brow * (B * B) + m.r * B, mr);
   else load_col<B, VT, AT>(M + (size_t)m.brow * (B * B), m.r, mr);
   AT out = AT(0);
 #pragma unroll
   for (int c = 0; c < B; ++c) out += mr[c] * fv[c];
-  const size_t o = (size_t)m.brow * B + m.r;
-  fin[o] = (XT)r[o];
+  fin[o] = ri;
   x[o] = (XT)out;
 }
 

@@ -290,7 +290,7 @@ def test_schur_import_rejects_mismatched_levels():
 FMT = {gb.GBS_FP32: "fp32", gb.GBS_BF16: "bf16"}
 
 
-@pytest.mark.parametrize("fmt", ["0", "1", "2", "3", "3s", "3d", "3w", "1b", "3o"])
+@pytest.mark.parametrize("fmt", ["0", "1", "2", "2c", "3", "3s", "3d", "3w", "1b", "3o"])
 @pytest.mark.parametrize("precision", [gb.GBS_FP32, gb.GBS_BF16])
 def test_mixed_vcycle_matches_oracle_on_cast_hierarchy(precision, fmt, monkeypatch):
     """Mixed forms (Section 4, Listing V4; BF16 storage with FP32
@@ -301,13 +301,15 @@ def test_mixed_vcycle_matches_oracle_on_cast_hierarchy(precision, fmt, monkeypat
     vector storage: a few units of 2^-24 per operation over the levels, so
     1e-5 relative in the max norm for both forms.  Formats 2 and 3 put
     every level in scalar CSR and in slices (the staged bulk-copy
-    kernels, or the direct ones where every slice is uniform); 3s / 3d
+    kernels, or the direct ones where every slice is uniform; plain CSR
+    with long rows streams 16-byte chunks, 2c keeps strided lanes); 3s / 3d
     send every sliced operator to the staged / direct kernels; 1b forces
     block-row slices on every block level."""
     monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt[0])
     monkeypatch.setenv("GBS_BSELL", "1" if fmt.endswith("b") else "0")
     monkeypatch.setenv("GBS_SELL_SORT", "1" if fmt.endswith("o") else "0")
     monkeypatch.setenv("GBS_SELL_GROUP", "0" if fmt.endswith("w") else "1")
+    monkeypatch.setenv("GBS_CSR_CHUNK", "0" if fmt.endswith("c") else "1")
     if fmt[1:] in ("s", "d"):
         monkeypatch.setenv("GBS_SELL_DIRECT", "0" if fmt.endswith("s") else "1")
     s = si.make_system("c2", N=10)
