@@ -360,9 +360,11 @@ __global__ void __launch_bounds__(SELL_WARPS * 32, 2)
 // column straight from global memory, four columns in flight per lane, at
 // up to 32 warps per SM.
 //
-// (Measured alternative that lost: each lane loading one column's offset
+// (Measured alternatives that lost: each lane loading one column's offset
 // and mask once and the warp broadcasting them by shuffles, in batches of
-// 8 columns -- C2 outer SpMV 43.7 us against 38.3.)
+// 8 columns -- C2 outer SpMV 43.7 us against 38.3; batches of 4 columns
+// whose offset, value and x loads issue in order through volatile PTX --
+// 40.3 us against 34.6 with one warp per 32-node group.)
 template <class VT, class XT, class AT>
 __device__ __forceinline__ AT sell_row_dot_direct(const DevSell<VT>& A, const XT* __restrict__ x, int q,
                                                   int lane, int64_t row) {
