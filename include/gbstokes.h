@@ -137,6 +137,16 @@ typedef struct {
                              0..40); the solve then returns GBS_ERR_CUDA.  Small
                              values exist to test that path: the copies still
                              land before the kernel returns */
+  int32_t iso_blocks;     /* 1 (default): a hierarchy level whose every block --
+                             of A_l, P_l, R_l and the smoother -- is a scalar
+                             multiple of the identity (checked exactly; the
+                             velocity hierarchy of a scalar-viscosity Stokes
+                             system is) is stored as the scalar matrix S with
+                             A_l = S (x) I_B, one value and one column a block,
+                             and each product applies S to the B interleaved
+                             components at once (unless level_format is 1);
+                             0: such levels follow level_format like any
+                             other */
 } gbs_params;
 
 typedef struct {
@@ -240,7 +250,9 @@ gbs_status gbs_outer_format(const gbs_hierarchy* h, int32_t* format, int64_t* st
  * measurement): *format = 0 block CSR, 1 scalar CSR of the nonzeros, 2
  * those nonzeros in 32-node component slices, 3 block-row slices; plus 4
  * when the level fuses its zero-guess smoothing step with the residual
- * (x = M f, r = f - (A M) f in one pass).  Host only. */
+ * (x = M f, r = f - (A M) f in one pass); plus 8 when the level runs as
+ * S (x) I_B (iso_blocks: the layout code then describes S, whose rows are
+ * the nodes).  Host only. */
 gbs_status gbs_level_format(const gbs_hierarchy* h, int32_t which, int32_t level,
                             int32_t* format);
 

@@ -67,6 +67,7 @@ class Params(ctypes.Structure):
         ("ilut_p", ctypes.c_double), ("ilut_tau", ctypes.c_double),
         ("ilut_sweeps", ctypes.c_int32), ("ilut_omega", ctypes.c_double),
         ("gmres_reorth", ctypes.c_int32), ("wait_log2", ctypes.c_int32),
+        ("iso_blocks", ctypes.c_int32),
     ]
 
 
@@ -458,6 +459,15 @@ def level_format(H: Hierarchy, which: int, level: int):
     f = ctypes.c_int32()
     _check(load_library().gbs_level_format(H.handle, which, level, ctypes.byref(f)))
     return LEVEL_LAYOUTS[f.value & 3], bool(f.value & 4)
+
+
+def level_iso(H: Hierarchy, which: int, level: int) -> bool:
+    """Whether level `level` of AMG `which` runs as S (x) I_B: its blocks are
+    multiples of the identity and one scalar operator acts on the B
+    interleaved components (gbs_params.iso_blocks)."""
+    f = ctypes.c_int32()
+    _check(load_library().gbs_level_format(H.handle, which, level, ctypes.byref(f)))
+    return bool(f.value & 8)
 
 
 OUTER_FORMATS = ("block", "csr", "sliced")

@@ -22,6 +22,7 @@
 #include <cstdlib>
 
 #include "device.hpp"
+#include "iso.cuh"
 #include "kernels.cuh"
 #include "sell.cuh"
 
@@ -61,6 +62,29 @@ std::vector<VT> cast_vec(const std::vector<double>& v) {
   return o;
 }
 
+// The chunk-streaming products (group_row_fwd) read whole 16-byte-aligned
+// chunks of a level's value array and, for scalar rows, of its column
+// array, and gather x at every column of a chunk: the last chunk reaches up
+// to 16 bytes past the last entry.  Uploads therefore pad both arrays to a
+// multiple of CHUNK_PAD entries (at least one chunk) with value 0 and
+// column 0, so every chunk lies inside its allocation and every gathered
+// column is a valid index.
+constexpr size_t CHUNK_PAD = 8;   // entries in 16 bytes of 2-byte values
+inline size_t chunk_padded(size_t n) {
+  return std::max<size_t>(CHUNK_PAD, (n + CHUNK_PAD - 1) / CHUNK_PAD * CHUNK_PAD);
+}
+inline std::vector<int32_t> padded_cols(const std::vector<int32_t>& c) {
+  std::vector<int32_t> o(chunk_padded(c.size()), 0);
+  std::copy(c.begin(), c.end(), o.begin());
+  return o;
+}
+template <class VT>
+std::vector<VT> padded_vals(const std::vector<double>& v) {
+  std::vector<VT> o = cast_vec<VT>(v);
+  o.resize(chunk_padded(v.size()), cast_host<VT>(0.0));
+  return o;
+}
+
 template <class VT, class AT>
 DevBsr<VT> upload_bsr(Arena& ar, const HBsr& H, bool with_tmap, cudaStream_t s,
                       std::vector<std::vector<VT>>& keep) {
@@ -68,8 +92,9 @@ DevBsr<VT> upload_bsr(Arena& ar, const HBsr& H, bool with_tmap, cudaStream_t s,
   d.nbr = H.nbr;
   d.nbc = H.nbc;
   d.rp = ar.upload(H.ptr.data(), H.ptr.size(), s);
-  d.col = ar.upload(H.col.data(), H.col.size(), s);
-  keep.push_back(cast_vec<VT>(H.val));
+  const std::vector<int32_t> cp = padded_cols(H.col);
+  d.col = ar.upload(cp.data(), cp.size(), s);
+  keep.push_back(padded_vals<VT>(H.val));
   d.val = ar.upload(keep.back().data(), keep.back().size(), s);
   if (H.nnzb() * H.br * H.bc >= (int64_t)INT32_MAX)
     throw SetupError{"a level holds 2^31 or more block values (int32 element indices)"};
@@ -108,8 +133,9 @@ DevCsr<VT> upload_csr(Arena& ar, const HCsr& C, cudaStream_t s, std::vector<std:
   DevCsr<VT> d;
   d.n = C.n;
   d.rp = ar.upload(C.ptr.data(), C.ptr.size(), s);
-  d.col = ar.upload(C.col.data(), C.col.size(), s);
-  keep.push_back(cast_vec<VT>(C.val));
+  const std::vector<int32_t> cp = padded_cols(C.col);   // see CHUNK_PAD
+  d.col = ar.upload(cp.data(), cp.size(), s);
+  keep.push_back(padded_vals<VT>(C.val));
   d.val = ar.upload(keep.back().data(), keep.back().size(), s);
   d.S = csr_split(C.n, (int64_t)C.col.size());
   if (const char* e = std::getenv("GBS_SPMV_SPLIT")) {
@@ -207,6 +233,15 @@ inline int use_sell(const HCsr& C, int B, int level_format) {
     if (e[0] == '1' && pad > 0.01) return 2;
   if (f == 3) return 1;
   return pad <= 0.10 ? 1 : 0;   // 0.4 measured slower in every form
+}
+
+// Stored entries of the slices that carry explicit columns (a uniform
+// slice's entries need no column load in the direct kernels).
+inline int64_t explicit_entries(const HSell& S) {
+  int64_t e = 0;
+  for (int q = 0; q < S.nslices; ++q)
+    if (S.cinfo[q] >= 0) e += (int64_t)(S.off[q + 1] - S.off[q]) * 32;
+  return e;
 }
 
 template <class VT>
@@ -463,6 +498,107 @@ void mapply(int B, int nbr, const VT* M, const XT* f, XT* x, cudaStream_t s) {
   GBS_LAUNCH_CHECK();
 }
 
+// ---- levels stored as S (x) I_B (iso.cuh): NV = B interleaved components
+template <int NV, int MODE, class VT, class XT, class YT, class AT>
+void iso_csr_spmv_nv(const DevCsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
+#define GBS_ISO(SS) \
+  k_iso_csr_spmv<NV, SS, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<1, SS>(A.n)), 256, 0, s>>>(A, x, f, y)
+  switch (A.S) {
+    case 2: GBS_ISO(2); break;
+    case 4: GBS_ISO(4); break;
+    case 8: GBS_ISO(8); break;
+    default: GBS_ISO(1);
+  }
+#undef GBS_ISO
+}
+// MODE SET / RESID / ADD with S in slices (sl) or plain CSR.
+template <int MODE, class VT, class XT, class YT, class AT>
+void iso_spmv(int NV, const DevCsr<VT>& Ac, const DevSell<VT>& As, bool sl, const XT* x,
+              const YT* f, YT* y, cudaStream_t s) {
+  if (sl) {
+    if (As.n == 0) return;
+    const unsigned g = grid_for((int64_t)As.nslices * 32);
+    switch (NV) {
+      case 2: k_iso_sell_spmv<2, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(As, x, f, y); break;
+      case 3: k_iso_sell_spmv<3, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(As, x, f, y); break;
+      case 4: k_iso_sell_spmv<4, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(As, x, f, y); break;
+    }
+  } else {
+    if (Ac.n == 0) return;
+    switch (NV) {
+      case 2: iso_csr_spmv_nv<2, MODE, VT, XT, YT, AT>(Ac, x, f, y, s); break;
+      case 3: iso_csr_spmv_nv<3, MODE, VT, XT, YT, AT>(Ac, x, f, y, s); break;
+      case 4: iso_csr_spmv_nv<4, MODE, VT, XT, YT, AT>(Ac, x, f, y, s); break;
+    }
+  }
+  GBS_LAUNCH_CHECK();
+}
+template <int NV, class VT, class XT, class AT, class OT>
+void iso_relax_nv(const DevCsr<VT>& Ac, const DevSell<VT>& As, bool sl, const VT* M, const XT* f,
+                  const XT* x, OT* xo, cudaStream_t s) {
+  if (sl) {
+    k_iso_sell_relax<NV, VT, XT, AT, OT>
+        <<<grid_for((int64_t)As.nslices * 32), 256, 0, s>>>(As, M, f, x, xo);
+    return;
+  }
+#define GBS_ISO(SS) \
+  k_iso_csr_relax<NV, SS, VT, XT, AT, OT><<<grid_for(row_threads_s<1, SS>(Ac.n)), 256, 0, s>>>(Ac, M, f, x, xo)
+  switch (Ac.S) {
+    case 2: GBS_ISO(2); break;
+    case 4: GBS_ISO(4); break;
+    case 8: GBS_ISO(8); break;
+    default: GBS_ISO(1);
+  }
+#undef GBS_ISO
+}
+// xo = x + (diag(m) (x) I) (f - (S (x) I) x); OT as in sell_relax.
+template <class VT, class XT, class AT, class OT = XT>
+void iso_relax(int NV, const DevCsr<VT>& Ac, const DevSell<VT>& As, bool sl, const VT* M,
+               const XT* f, const XT* x, OT* xo, cudaStream_t s) {
+  if (sl ? As.n == 0 : Ac.n == 0) return;
+  switch (NV) {
+    case 2: iso_relax_nv<2, VT, XT, AT, OT>(Ac, As, sl, M, f, x, xo, s); break;
+    case 3: iso_relax_nv<3, VT, XT, AT, OT>(Ac, As, sl, M, f, x, xo, s); break;
+    case 4: iso_relax_nv<4, VT, XT, AT, OT>(Ac, As, sl, M, f, x, xo, s); break;
+  }
+  GBS_LAUNCH_CHECK();
+}
+template <class VT, class XT, class AT>
+void iso_presmooth(int NV, const DevSell<VT>& AM, const VT* M, const XT* f, XT* x, XT* r,
+                   cudaStream_t s) {
+  if (AM.n == 0) return;
+  const unsigned g = grid_for((int64_t)AM.nslices * 32);
+  switch (NV) {
+    case 2: k_iso_sell_presmooth<2, VT, XT, AT><<<g, 256, 0, s>>>(AM, M, f, x, r); break;
+    case 3: k_iso_sell_presmooth<3, VT, XT, AT><<<g, 256, 0, s>>>(AM, M, f, x, r); break;
+    case 4: k_iso_sell_presmooth<4, VT, XT, AT><<<g, 256, 0, s>>>(AM, M, f, x, r); break;
+  }
+  GBS_LAUNCH_CHECK();
+}
+template <class VT, class XT, class AT>
+void iso_mapply(int NV, int64_t n, const VT* M, const XT* f, XT* x, cudaStream_t s) {
+  if (n == 0) return;
+  const unsigned g = grid_for(n);
+  switch (NV) {
+    case 2: k_iso_mapply<2, VT, XT, AT><<<g, 256, 0, s>>>(n, M, f, x); break;
+    case 3: k_iso_mapply<3, VT, XT, AT><<<g, 256, 0, s>>>(n, M, f, x); break;
+    case 4: k_iso_mapply<4, VT, XT, AT><<<g, 256, 0, s>>>(n, M, f, x); break;
+  }
+  GBS_LAUNCH_CHECK();
+}
+template <class VT, class XT, class AT>
+void iso_cast_mapply(int NV, int64_t n, const VT* M, const double* r64, XT* fin, XT* x,
+                     cudaStream_t s) {
+  if (n == 0) return;
+  const unsigned g = grid_for(n);
+  switch (NV) {
+    case 2: k_iso_cast_mapply<2, VT, XT, AT><<<g, 256, 0, s>>>(n, M, r64, fin, x); break;
+    case 3: k_iso_cast_mapply<3, VT, XT, AT><<<g, 256, 0, s>>>(n, M, r64, fin, x); break;
+    case 4: k_iso_cast_mapply<4, VT, XT, AT><<<g, 256, 0, s>>>(n, M, r64, fin, x); break;
+  }
+  GBS_LAUNCH_CHECK();
+}
+
 template <class TI, class TO>
 void cast(int64_t n, const TI* in, TO* out, cudaStream_t s) {
   if (n == 0) return;
@@ -491,6 +627,13 @@ struct DevAmg {
     int64_t nnz_Li = 0, nnz_Ui = 0;
     bool a_csr = false, p_csr = false, r_csr = false;
     bool a_sell = false, p_sell = false, r_sell = false;
+    // A = S (x) I_B (every block of A, P, R and M a multiple of I_B): Ac/As,
+    // Pc/Ps, Rc/Rs hold S and the scalar P and R (one row per node), M one
+    // value per node, AcT = S^T for the transposed cycle (iso.cuh)
+    bool iso = false;
+    DevCsr<VT> AcT;
+    int64_t xsl_A = 0, xsl_P = 0, xsl_R = 0, xsl_AM = 0;  // slices: entries with column loads
+    bool dir_A = false, dir_P = false, dir_R = false;       // slices read by direct kernels
     DevBSell<VT> Ab;                    // block-row slices of A (FP64 block levels)
     bool a_bsell = false;
     int64_t slots_Ab = 0;
@@ -529,83 +672,90 @@ struct DevAmg {
       const HLevel& h = H.levels[l];
       Lev L;
       L.n = (int64_t)h.A.nbr * B;
-      L.a_csr = use_scalar_csr(h.A, o.level_format);
-      L.p_csr = use_scalar_csr(h.P, o.level_format);
-      L.r_csr = use_scalar_csr(h.R, o.level_format);
-      // the block form of A stays resident when the adjoint may need A^T
-      if (!L.a_csr || o.tmaps) L.A = upload_bsr<VT, AT>(ar, h.A, o.tmaps, s, keep);
-      else { L.A.nbr = h.A.nbr; L.A.nbc = h.A.nbc; }
-      if (!L.a_csr && use_bsell<AT>(h.A, L.A.G)) {
-        const HBSell Sb = to_bsell(h.A, BSELL_WINDOW);
-        L.Ab = upload_bsell<VT>(ar, Sb, s, keep);
-        L.a_bsell = true;
-        L.slots_Ab = (int64_t)Sb.col.size();
-        GBS_CUDA(cudaStreamSynchronize(s));  // Sb's host arrays die here
-      }
-      // scalar CSR, as plain rows or in slices
-      auto scalar = [&](const HBsr& Hm, DevCsr<VT>& dc, DevSell<VT>& ds, bool& sl, int64_t& nnz,
-                        int64_t& slots, int64_t& nsl) {
-        HCsr c = to_scalar_csr(Hm);
-        nnz = (int64_t)c.col.size();
-        const int how = use_sell(c, B, o.level_format);
-        sl = how != 0;
-        if (sl) {
-          const HSell S = to_sell(c, B, how == 2);
-          slots = (int64_t)S.col.size();
-          nsl = S.nslices;
-          ds = upload_sell<VT>(ar, S, o.err, o.wait_cycles, s, keep);
-          GBS_CUDA(cudaStreamSynchronize(s));  // S's host arrays die here
-        } else {
-          dc = upload_csr<VT>(ar, c, s, keep);
+      if (iso_level(h, o)) {
+        build_iso(h, o, L, s, keep);
+      } else {
+        L.a_csr = use_scalar_csr(h.A, o.level_format);
+        L.p_csr = use_scalar_csr(h.P, o.level_format);
+        L.r_csr = use_scalar_csr(h.R, o.level_format);
+        // the block form of A stays resident when the adjoint may need A^T
+        if (!L.a_csr || o.tmaps) L.A = upload_bsr<VT, AT>(ar, h.A, o.tmaps, s, keep);
+        else { L.A.nbr = h.A.nbr; L.A.nbc = h.A.nbc; }
+        if (!L.a_csr && use_bsell<AT>(h.A, L.A.G)) {
+          const HBSell Sb = to_bsell(h.A, BSELL_WINDOW);
+          L.Ab = upload_bsell<VT>(ar, Sb, s, keep);
+          L.a_bsell = true;
+          L.slots_Ab = (int64_t)Sb.col.size();
+          GBS_CUDA(cudaStreamSynchronize(s));  // Sb's host arrays die here
         }
-      };
-      if (L.a_csr) scalar(h.A, L.Ac, L.As, L.a_sell, L.nnz_A, L.slots_A, L.sl_A);
-      if (L.p_csr) scalar(h.P, L.Pc, L.Ps, L.p_sell, L.nnz_P, L.slots_P, L.sl_P);
-      else L.Pm = upload_bsr<VT, AT>(ar, h.P, false, s, keep);
-      if (L.r_csr) scalar(h.R, L.Rc, L.Rs, L.r_sell, L.nnz_R, L.slots_R, L.sl_R);
-      else L.R = upload_bsr<VT, AT>(ar, h.R, false, s, keep);
-      keep.push_back(cast_vec<VT>(h.M));
-      L.M = ar.upload(keep.back().data(), keep.back().size(), s);
-      if (!h.ilu.d.empty()) {
-        L.ilu = true;
-        HCsr Us = h.ilu.U;
-        for (int i = 0; i < Us.n; ++i)
-          for (int k = Us.ptr[i]; k < Us.ptr[i + 1]; ++k) Us.val[k] /= h.ilu.d[i];
-        std::vector<double> di(h.ilu.d.size());
-        for (size_t i = 0; i < di.size(); ++i) di[i] = 1.0 / h.ilu.d[i];
-        L.Li = upload_csr<VT>(ar, h.ilu.L, s, keep);
-        L.Ui = upload_csr<VT>(ar, Us, s, keep);
-        if (o.tmaps) {
-          L.LiT = upload_csr<VT>(ar, transpose(h.ilu.L), s, keep);
-          L.UiT = upload_csr<VT>(ar, transpose(Us), s, keep);
-        }
-        keep.push_back(cast_vec<VT>(di));
-        L.dinv = ar.upload(keep.back().data(), keep.back().size(), s);
-        L.wa = ar.alloc<ST>(L.n);
-        L.wb = ar.alloc<ST>(L.n);
-        L.wc = ar.alloc<ST>(L.n);
-        L.nnz_Li = (int64_t)h.ilu.L.col.size();
-        L.nnz_Ui = (int64_t)h.ilu.U.col.size();
-        GBS_CUDA(cudaStreamSynchronize(s));  // host staging (Us, transposes) dies here
-      }
-      if (use_fused<AT>(h, o) && (L.a_sell || L.a_bsell)) {
-        const HBsr AM = scale_columns(h.A, h.M);
-        if (L.a_bsell) {
-          const HBSell Sb = to_bsell(AM, BSELL_WINDOW);
-          L.AMb = upload_bsell<VT>(ar, Sb, s, keep);
-          L.slots_AM = (int64_t)Sb.col.size();
-          L.fused = 2;
-          GBS_CUDA(cudaStreamSynchronize(s));
-        } else {
-          const HCsr c = to_scalar_csr(AM);
+        // scalar CSR, as plain rows or in slices
+        auto scalar = [&](const HBsr& Hm, DevCsr<VT>& dc, DevSell<VT>& ds, bool& sl, int64_t& nnz,
+                          int64_t& slots, int64_t& nsl, int64_t& xsl, bool& dir) {
+          HCsr c = to_scalar_csr(Hm);
+          nnz = (int64_t)c.col.size();
           const int how = use_sell(c, B, o.level_format);
-          if (how) {
-            const HSell Sa = to_sell(c, B, how == 2);
-            L.AMs = upload_sell<VT>(ar, Sa, o.err, o.wait_cycles, s, keep);
-            L.slots_AM = (int64_t)Sa.col.size();
-            L.sl_AM = Sa.nslices;
-            L.fused = 1;
+          sl = how != 0;
+          if (sl) {
+            const HSell S = to_sell(c, B, how == 2);
+            slots = (int64_t)S.col.size();
+            nsl = S.nslices;
+            xsl = explicit_entries(S);
+            ds = upload_sell<VT>(ar, S, o.err, o.wait_cycles, s, keep);
+            dir = sell_direct<VT, AT>(ds);
+            GBS_CUDA(cudaStreamSynchronize(s));  // S's host arrays die here
+          } else {
+            dc = upload_csr<VT>(ar, c, s, keep);
+          }
+        };
+        if (L.a_csr) scalar(h.A, L.Ac, L.As, L.a_sell, L.nnz_A, L.slots_A, L.sl_A, L.xsl_A, L.dir_A);
+        if (L.p_csr) scalar(h.P, L.Pc, L.Ps, L.p_sell, L.nnz_P, L.slots_P, L.sl_P, L.xsl_P, L.dir_P);
+        else L.Pm = upload_bsr<VT, AT>(ar, h.P, false, s, keep);
+        if (L.r_csr) scalar(h.R, L.Rc, L.Rs, L.r_sell, L.nnz_R, L.slots_R, L.sl_R, L.xsl_R, L.dir_R);
+        else L.R = upload_bsr<VT, AT>(ar, h.R, false, s, keep);
+        keep.push_back(cast_vec<VT>(h.M));
+        L.M = ar.upload(keep.back().data(), keep.back().size(), s);
+        if (!h.ilu.d.empty()) {
+          L.ilu = true;
+          HCsr Us = h.ilu.U;
+          for (int i = 0; i < Us.n; ++i)
+            for (int k = Us.ptr[i]; k < Us.ptr[i + 1]; ++k) Us.val[k] /= h.ilu.d[i];
+          std::vector<double> di(h.ilu.d.size());
+          for (size_t i = 0; i < di.size(); ++i) di[i] = 1.0 / h.ilu.d[i];
+          L.Li = upload_csr<VT>(ar, h.ilu.L, s, keep);
+          L.Ui = upload_csr<VT>(ar, Us, s, keep);
+          if (o.tmaps) {
+            L.LiT = upload_csr<VT>(ar, transpose(h.ilu.L), s, keep);
+            L.UiT = upload_csr<VT>(ar, transpose(Us), s, keep);
+          }
+          keep.push_back(cast_vec<VT>(di));
+          L.dinv = ar.upload(keep.back().data(), keep.back().size(), s);
+          L.wa = ar.alloc<ST>(L.n);
+          L.wb = ar.alloc<ST>(L.n);
+          L.wc = ar.alloc<ST>(L.n);
+          L.nnz_Li = (int64_t)h.ilu.L.col.size();
+          L.nnz_Ui = (int64_t)h.ilu.U.col.size();
+          GBS_CUDA(cudaStreamSynchronize(s));  // host staging (Us, transposes) dies here
+        }
+        if (use_fused<AT>(h, o) && (L.a_sell || L.a_bsell)) {
+          const HBsr AM = scale_columns(h.A, h.M);
+          if (L.a_bsell) {
+            const HBSell Sb = to_bsell(AM, BSELL_WINDOW);
+            L.AMb = upload_bsell<VT>(ar, Sb, s, keep);
+            L.slots_AM = (int64_t)Sb.col.size();
+            L.fused = 2;
             GBS_CUDA(cudaStreamSynchronize(s));
+          } else {
+            const HCsr c = to_scalar_csr(AM);
+            const int how = use_sell(c, B, o.level_format);
+            if (how) {
+              const HSell Sa = to_sell(c, B, how == 2);
+              L.AMs = upload_sell<VT>(ar, Sa, o.err, o.wait_cycles, s, keep);
+              L.slots_AM = (int64_t)Sa.col.size();
+              L.sl_AM = Sa.nslices;
+              L.xsl_AM = explicit_entries(Sa);
+              L.fused = 1;
+              GBS_CUDA(cudaStreamSynchronize(s));
+            }
           }
         }
       }
@@ -638,11 +788,72 @@ struct DevAmg {
     GBS_CUDA(cudaStreamSynchronize(s));  // host staging buffers die here
   }
 
+  // A level stored as S (x) I_B: every block of A, P, R and of the smoother
+  // is a multiple of the identity (checked bitwise; not for ILUT levels,
+  // nor under level_format 1, which keeps every level in block form).
+  // GBS_ISO=0 / 1 overrides iso_blocks (measurement and tests).
+  bool iso_level(const HLevel& h, const PrecondOptions& o) const {
+    bool on = o.iso;
+    if (const char* e = std::getenv("GBS_ISO")) on = e[0] != '0';
+    if (level_format_of(o.level_format) == 1) on = false;
+    return on && B > 1 && h.ilu.d.empty() && !h.M.empty() && is_iso(h.A) && is_iso(h.P) &&
+           is_iso(h.R) && is_iso_blocks(h.M, B);
+  }
+  void build_iso(const HLevel& h, const PrecondOptions& o, Lev& L, cudaStream_t s,
+                 std::vector<std::vector<VT>>& keep) {
+    L.iso = true;
+    L.A.nbr = h.A.nbr;
+    L.A.nbc = h.A.nbc;
+    L.a_csr = L.p_csr = L.r_csr = true;
+    L.dir_A = L.dir_P = L.dir_R = true;   // the iso kernels load every slice directly
+    // S, P and R as scalar CSR with one row per node, in slices where
+    // they pad little (use_sell with one component a node)
+    auto scalar = [&](const HCsr& c, DevCsr<VT>& dc, DevSell<VT>& ds, bool& sl, int64_t& nnz,
+                      int64_t& slots, int64_t& nsl, int64_t& xsl) {
+      nnz = (int64_t)c.col.size();
+      const int how = use_sell(c, 1, o.level_format);
+      sl = how != 0;
+      if (sl) {
+        const HSell S = to_sell(c, 1, how == 2);
+        slots = (int64_t)S.col.size();
+        nsl = S.nslices;
+        xsl = explicit_entries(S);
+        ds = upload_sell<VT>(ar, S, o.err, o.wait_cycles, s, keep);
+        GBS_CUDA(cudaStreamSynchronize(s));  // S's host arrays die here
+      } else {
+        dc = upload_csr<VT>(ar, c, s, keep);
+      }
+    };
+    const HCsr Sa = iso_scalar(h.A);
+    scalar(Sa, L.Ac, L.As, L.a_sell, L.nnz_A, L.slots_A, L.sl_A, L.xsl_A);
+    scalar(iso_scalar(h.P), L.Pc, L.Ps, L.p_sell, L.nnz_P, L.slots_P, L.sl_P, L.xsl_P);
+    scalar(iso_scalar(h.R), L.Rc, L.Rs, L.r_sell, L.nnz_R, L.slots_R, L.sl_R, L.xsl_R);
+    if (o.tmaps) {
+      L.AcT = upload_csr<VT>(ar, transpose(Sa), s, keep);
+      GBS_CUDA(cudaStreamSynchronize(s));
+    }
+    keep.push_back(cast_vec<VT>(iso_diag(h.M, B)));
+    L.M = ar.upload(keep.back().data(), keep.back().size(), s);
+    if (use_fused<AT>(h, o) && L.a_sell) {
+      const HCsr c = iso_scalar(scale_columns(h.A, h.M));
+      const int how = use_sell(c, 1, o.level_format);
+      if (how) {
+        const HSell Sm = to_sell(c, 1, how == 2);
+        L.AMs = upload_sell<VT>(ar, Sm, o.err, o.wait_cycles, s, keep);
+        L.slots_AM = (int64_t)Sm.col.size();
+        L.sl_AM = Sm.nslices;
+        L.xsl_AM = explicit_entries(Sm);
+        L.fused = 1;
+        GBS_CUDA(cudaStreamSynchronize(s));
+      }
+    }
+  }
+
   int64_t n0() const { return lev[0].n; }
   int layout(size_t l) const {
     const Lev& L = lev[l];
     const int base = L.a_bsell ? 3 : L.a_sell ? 2 : L.a_csr ? 1 : 0;
-    return base + (L.fused ? 4 : 0);
+    return base + (L.fused ? 4 : 0) + (L.iso ? 8 : 0);
   }
 
   // z = S r with S the approximate (LU)^-1 of an ILUT level (S^T when TR):
@@ -676,6 +887,11 @@ struct DevAmg {
   // r = f - A_l x (A^T when TR)
   template <bool TR>
   void resid(Lev& L, const ST* x, const ST* f, ST* r, cudaStream_t s) {
+    if (L.iso) {   // (S (x) I)^T = S^T (x) I
+      if (TR) iso_spmv<SPMV_RESID, VT, ST, ST, AT>(B, L.AcT, L.As, false, x, f, r, s);
+      else iso_spmv<SPMV_RESID, VT, ST, ST, AT>(B, L.Ac, L.As, L.a_sell, x, f, r, s);
+      return;
+    }
     const bool acsr = L.a_csr && !TR;   // A^T goes through the block form's transpose map
     if (L.a_bsell && !TR) bsell_spmv<SPMV_RESID, VT, ST, ST, AT>(B, L.Ab, x, f, r, s);
     else if (acsr && L.a_sell) sell_spmv<SPMV_RESID, VT, ST, ST, AT>(L.As, x, f, r, s);
@@ -692,6 +908,9 @@ struct DevAmg {
       const ST* z = ilu_apply<TR>(L, L.r, s);
       k_vaxpy<ST><<<grid_for(L.n), 256, 0, s>>>(L.n, xin, (ST)ilu_omega, z, xout);
       GBS_LAUNCH_CHECK();
+    } else if (L.iso) {   // diag(m) (x) I is symmetric: the transposed sweep uses S^T only
+      if (TR) iso_relax<VT, ST, AT>(B, L.AcT, L.As, false, L.M, f, xin, xout, s);
+      else iso_relax<VT, ST, AT>(B, L.Ac, L.As, L.a_sell, L.M, f, xin, xout, s);
     } else if (L.a_bsell && !TR) {
       bsell_relax<VT, ST, AT>(B, L.Ab, L.M, f, xin, xout, s);
     } else if (acsr && L.a_sell) {
@@ -705,6 +924,10 @@ struct DevAmg {
 
   // x = M f and r = f - A x (zero-guess pre-smoothing + residual, fused).
   void presmooth_resid(Lev& L, const ST* f, ST* x, ST* r, cudaStream_t s) {
+    if (L.iso) {
+      iso_presmooth<VT, ST, AT>(B, L.AMs, L.M, f, x, r, s);
+      return;
+    }
     if (L.fused == 2) {
       const unsigned g = grid_for((int64_t)L.AMb.nslices * 32);
       switch (B) {
@@ -766,6 +989,8 @@ struct DevAmg {
         have_r = true;
       } else if (r64) {
         cast_mapply<TR>(L, r64, const_cast<ST*>(f), x, s);   // f = (ST) r64 and x = M f
+      } else if (L.iso) {
+        iso_mapply<VT, ST, AT>(B, L.n, L.M, f, x, s);
       } else {
         mapply<TR, VT, ST, AT>(B, nb, L.M, f, x, s);
       }
@@ -779,15 +1004,21 @@ struct DevAmg {
     if (!have_r) resid<TR>(L, x, f, L.r, s);
     Lev& Cn = lev[l + 1];
     const ST* none = nullptr;
-    if (L.r_sell) sell_spmv<SPMV_SET, VT, ST, ST, AT>(L.Rs, L.r, none, Cn.f, s);
+    if (L.iso) iso_spmv<SPMV_SET, VT, ST, ST, AT>(B, L.Rc, L.Rs, L.r_sell, L.r, none, Cn.f, s);
+    else if (L.r_sell) sell_spmv<SPMV_SET, VT, ST, ST, AT>(L.Rs, L.r, none, Cn.f, s);
     else if (L.r_csr) csr_spmv<SPMV_SET, VT, ST, ST, AT>(L.Rc, L.r, none, Cn.f, s);
     else spmv<false, SPMV_SET, VT, ST, ST, AT>(B, L.R, L.r, none, Cn.f, s);
     cycle<TR>(l + 1, Cn.f, Cn.e, s);
-    if (L.p_sell) sell_spmv<SPMV_ADD, VT, ST, ST, AT>(L.Ps, Cn.e, none, x, s);
+    if (L.iso) iso_spmv<SPMV_ADD, VT, ST, ST, AT>(B, L.Pc, L.Ps, L.p_sell, Cn.e, none, x, s);
+    else if (L.p_sell) sell_spmv<SPMV_ADD, VT, ST, ST, AT>(L.Ps, Cn.e, none, x, s);
     else if (L.p_csr) csr_spmv<SPMV_ADD, VT, ST, ST, AT>(L.Pc, Cn.e, none, x, s);
     else spmv<false, SPMV_ADD, VT, ST, ST, AT>(B, L.Pm, Cn.e, none, x, s);
     for (int it = 0; it < post; ++it) {
       const bool last = it + 1 == post;
+      if (last && z64 && !TR && L.iso) {   // the last sweep writes the FP64 output
+        iso_relax<VT, ST, AT, double>(B, L.Ac, L.As, L.a_sell, L.M, f, x, z64, s);
+        return;
+      }
       if (last && z64 && !TR && L.a_csr && L.a_sell && !L.ilu) {
         // the last sweep writes the FP64 output (no cast pass)
         sell_relax<VT, ST, AT, double>(B, L.As, L.M, f, x, z64, s);
@@ -803,6 +1034,10 @@ struct DevAmg {
 
   template <bool TR>
   void cast_mapply(Lev& L, const double* r64, ST* fin, ST* x, cudaStream_t s) {
+    if (L.iso) {
+      iso_cast_mapply<VT, ST, AT>(B, L.n, L.M, r64, fin, x, s);
+      return;
+    }
     const int nb = L.A.nbr;
     switch (B) {
       case 1: k_cast_mapply<1, TR, VT, ST, AT><<<grid_for(row_threads<1>(nb)), 256, 0, s>>>(nb, L.M, r64, fin, x); break;
@@ -834,17 +1069,24 @@ struct DevAmg {
       const Lev& L = lev[l];
       const double nb = (double)L.A.nbr;
       const double nc = (double)(lev[l + 1].n / B);
+      // slices: values, columns where a kernel loads them (staged kernels
+      // stage every column; direct ones skip uniform slices), offsets
+      auto sliced = [&](int64_t slots, int64_t xsl, bool dir, int64_t nsl) {
+        return slots * sv + 4.0 * (dir ? xsl : slots) + 4 * (nsl + 1.0);
+      };
+      // scalar CSR rows: one per scalar row, or one per node (iso levels)
+      const double rows_f = L.iso ? nb : (double)L.n, rows_c = L.iso ? nc : nc * B;
       const double Abytes = L.a_bsell ? L.slots_Ab * (B * B * sv + 4) + 4.0 * L.Ab.nslices * (32 / B + 1)
-                            : L.a_sell ? L.slots_A * (sv + 4) + 4 * (L.sl_A + 1.0)
-                            : L.a_csr ? L.nnz_A * (sv + 4) + 4 * (L.n + 1.0)
+                            : L.a_sell ? sliced(L.slots_A, L.xsl_A, L.dir_A, L.sl_A)
+                            : L.a_csr ? L.nnz_A * (sv + 4) + 4 * (rows_f + 1.0)
                                       : L.nnzb_A * (B * B * sv + 4) + 4 * (nb + 1);
-      const double Pbytes = L.p_sell ? L.slots_P * (sv + 4) + 4 * (L.sl_P + 1.0)
-                            : L.p_csr ? L.nnz_P * (sv + 4) + 4 * (L.n + 1.0)
+      const double Pbytes = L.p_sell ? sliced(L.slots_P, L.xsl_P, L.dir_P, L.sl_P)
+                            : L.p_csr ? L.nnz_P * (sv + 4) + 4 * (rows_f + 1.0)
                                       : L.nnzb_P * (B * B * sv + 4) + 4 * (nb + 1);
-      const double Rbytes = L.r_sell ? L.slots_R * (sv + 4) + 4 * (L.sl_R + 1.0)
-                            : L.r_csr ? L.nnz_R * (sv + 4) + 4 * (nc * B + 1)
+      const double Rbytes = L.r_sell ? sliced(L.slots_R, L.xsl_R, L.dir_R, L.sl_R)
+                            : L.r_csr ? L.nnz_R * (sv + 4) + 4 * (rows_c + 1)
                                       : L.nnzb_R * (B * B * sv + 4) + 4 * (nc + 1);
-      const double Mbytes = nb * B * B * sv;
+      const double Mbytes = L.iso ? nb * sv : nb * B * B * sv;
       b += Abytes + 3 * L.n * sx;                               // resid (A, x, f, r)
       b += Rbytes + L.n * sx + lev[l + 1].n * sx;               // restrict (R, r, fc)
       b += Pbytes + lev[l + 1].n * sx + 2 * L.n * sx;           // prolong (P, ec, x rw)
@@ -864,7 +1106,7 @@ struct DevAmg {
         // mapply and the residual
         const double AMbytes = L.fused == 2
             ? L.slots_AM * (B * B * sv + 4) + 4.0 * L.AMb.nslices * (32 / B + 1)
-            : L.slots_AM * (sv + 4) + 4 * (L.sl_AM + 1.0);
+            : sliced(L.slots_AM, L.xsl_AM, true, L.sl_AM);
         b -= (Mbytes + 2 * L.n * sx) + (Abytes + 3 * L.n * sx);
         b += AMbytes + Mbytes + 3 * L.n * sx;
       }
@@ -919,7 +1161,7 @@ struct AmgPrecond final : DevPrecond {
       const auto& L = amg.lev[0];
       const bool deep = amg.lev.size() > 1 && !L.ilu;
       b += deep && amg.npre >= 1 ? n * (8 - sx) : n * (8 + sx);
-      b += deep && L.a_csr && L.a_sell ? n * (8 - sx) : n * (8 + sx);
+      b += deep && (L.iso || (L.a_csr && L.a_sell)) ? n * (8 - sx) : n * (8 + sx);
     }
     return b;
   }

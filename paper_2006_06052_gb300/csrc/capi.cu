@@ -136,6 +136,7 @@ void check_params(const gbs_params* p) {
   if (p->schur_order < 0 || p->schur_order > 1) throw SetupError{"schur_order must be 0 or 1"};
   if (p->gmres_reorth < 0 || p->gmres_reorth > 2) throw SetupError{"gmres_reorth must be 0, 1 or 2"};
   if (p->wait_log2 < 0 || p->wait_log2 > 40) throw SetupError{"wait_log2 must be in 0..40"};
+  if (p->iso_blocks < 0 || p->iso_blocks > 1) throw SetupError{"iso_blocks must be 0 or 1"};
 }
 
 AmgSetupParams amg_prm(const gbs_params* p, int relax) {
@@ -164,17 +165,20 @@ PrecondOptions pc_opts(const gbs_params* p) {
   o.ilut_sweeps = p->ilut_sweeps;
   o.ilut_omega = p->ilut_omega;
   o.wait_cycles = 1LL << p->wait_log2;
+  o.iso = p->iso_blocks != 0;
   return o;
 }
 
 void alloc_work(Handle& h, cudaStream_t s) {
   Arena& a = h.ar;
   const int64_t n = h.n;
-  h.Kval = a.upload(h.Kh.val.data(), h.Kh.val.size(), s);
+  const std::vector<double> kv = padded_vals<double>(h.Kh.val);   // see CHUNK_PAD
+  h.Kval = a.upload(kv.data(), kv.size(), s);
   h.K.nbr = h.Kh.nbr;
   h.K.nbc = h.Kh.nbc;
   h.K.rp = a.upload(h.Kh.ptr.data(), h.Kh.ptr.size(), s);
-  h.K.col = a.upload(h.Kh.col.data(), h.Kh.col.size(), s);
+  const std::vector<int32_t> kc = padded_cols(h.Kh.col);
+  h.K.col = a.upload(kc.data(), kc.size(), s);
   h.K.val = h.Kval;
   switch (h.B) {
     case 1: h.K.G = choose_group<1, double, double>(h.Kh.nbr, h.Kh.nnzb()); break;
@@ -1002,6 +1006,7 @@ gbs_status gbs_params_default(gbs_params* p) {
   p->ilut_omega = 1.0;
   p->gmres_reorth = 0;
   p->wait_log2 = 31;
+  p->iso_blocks = 1;
   return GBS_OK;
 }
 

@@ -104,6 +104,7 @@ struct PrecondOptions {
   long long wait_cycles = 1LL << 31;  // bound of a pipeline wait (SM clocks)
   int ilut_sweeps = 2;            // Jacobi sweeps per ILUT triangular solve
   double ilut_omega = 1.0;        // ILUT relaxation damping
+  bool iso = true;                // store levels of multiples of I_B as S (x) I_B (iso.cuh)
 };
 
 std::unique_ptr<DevPrecond> make_amg_precond(const HAmg& H, const PrecondOptions& o,

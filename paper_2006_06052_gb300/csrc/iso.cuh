@@ -1,0 +1,235 @@
+// Levels whose blocks are scalar multiples of the identity.
+//
+// When every stored block of a level operator is a_ij * I_B -- the
+// velocity block of a Stokes system with a scalar viscosity, whose B
+// components share every stencil coefficient, and therefore every
+// smoothed-aggregation level built from it (P_tent is identity blocks,
+// and products and inverses of a_ij * I_B blocks stay of that form) --
+// the operator is S (x) I_B for a scalar matrix S.  Such a level is
+// stored as S: one value and one column per block, where the scalar CSR
+// of the nonzeros stores B of each and the block form B*B values.  The
+// smoother is diag(m) (x) I_B, one value per node.
+//
+// One lane owns one node (row of S) and applies the row to the node's B
+// interleaved components at once: each value is loaded once for B FMAs,
+// the B gathered x entries of a column are adjacent, and the node's B
+// outputs are formed and stored by the same lane.  The arithmetic per
+// output is the block form's with the zero terms left out, so results
+// agree with it to rounding order.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace gbs {
+
+// x[j*NV .. j*NV + NV - 1] as AT.
+template <int NV, class XT, class AT>
+__device__ __forceinline__ void iso_gather(const XT* __restrict__ x, int64_t j, AT (&o)[NV]) {
+  load_run<NV, XT, AT, false>(x + j * NV, o);
+}
+
+// Row `row` of S over the entries k0 + s, k0 + s + S, ... times the NV
+// components of x.
+template <int NV, int S, class VT, class XT, class AT>
+__device__ __forceinline__ void iso_csr_row(const DevCsr<VT>& A, const XT* __restrict__ x,
+                                            int row, int s, AT (&acc)[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = AT(0);
+  const int k0 = A.rp[row], k1 = A.rp[row + 1];
+#pragma unroll 4
+  for (int k = k0 + s; k < k1; k += S) {
+    const AT a = cvt<AT>(__ldcs(A.val + k));
+    AT xv[NV];
+    iso_gather<NV, XT, AT>(x, __ldg(A.col + k), xv);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] += a * xv[v];
+  }
+}
+
+template <int NV, int MODE, class XT, class YT, class AT>
+__device__ __forceinline__ void iso_store(int64_t node, const AT (&acc)[NV],
+                                          const YT* __restrict__ f, YT* __restrict__ y) {
+  const size_t o = (size_t)node * NV;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if constexpr (MODE == SPMV_SET) y[o + v] = (YT)acc[v];
+    else if constexpr (MODE == SPMV_RESID) y[o + v] = (YT)(cvt<AT>(f[o + v]) - acc[v]);
+    else y[o + v] = (YT)(cvt<AT>(y[o + v]) + acc[v]);
+  }
+}
+
+// MODE SET / RESID / ADD: y = (S (x) I) x, f - (S (x) I) x, y + (S (x) I) x
+// with S in scalar CSR and S lanes per row.
+template <int NV, int S, int MODE, class VT, class XT, class YT, class AT>
+__global__ void __launch_bounds__(256, 4) k_iso_csr_spmv(DevCsr<VT> A, const XT* __restrict__ x,
+                                                      const YT* __restrict__ f,
+                                                      YT* __restrict__ y) {
+  RowMapS<1, S> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  const bool ok = m.lane_ok && m.brow < A.n;
+  AT acc[NV];
+  if (ok) iso_csr_row<NV, S, VT, XT, AT>(A, x, m.brow, m.s, acc);
+  else
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = AT(0);
+  if constexpr (S > 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = split_reduce<1, S, AT>(acc[v]);
+  }
+  if (!ok || m.s != 0) return;
+  iso_store<NV, MODE, XT, YT, AT>(m.brow, acc, f, y);
+}
+
+// xo = x + m .* (f - (S (x) I) x), m one smoother value per node.
+template <int NV, int S, class VT, class XT, class AT, class OT = XT>
+__global__ void __launch_bounds__(256, 4) k_iso_csr_relax(DevCsr<VT> A, const VT* __restrict__ M,
+                                                       const XT* __restrict__ f,
+                                                       const XT* __restrict__ x,
+                                                       OT* __restrict__ xo) {
+  RowMapS<1, S> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  const bool ok = m.lane_ok && m.brow < A.n;
+  AT acc[NV];
+  if (ok) iso_csr_row<NV, S, VT, XT, AT>(A, x, m.brow, m.s, acc);
+  else
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = AT(0);
+  if constexpr (S > 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = split_reduce<1, S, AT>(acc[v]);
+  }
+  if (!ok || m.s != 0) return;
+  const AT mi = cvt<AT>(M[m.brow]);
+  const size_t o = (size_t)m.brow * NV;
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    xo[o + v] = (OT)(XT)(cvt<AT>(x[o + v]) + mi * (cvt<AT>(f[o + v]) - acc[v]));
+}
+
+// Row of lane `lane` of slice q of S (32 consecutive nodes a slice) times
+// the NV components of x; a uniform slice gathers at node + offset with no
+// column loads.
+template <int NV, class VT, class XT, class AT>
+__device__ __forceinline__ void iso_sell_row(const DevSell<VT>& A, const XT* __restrict__ x, int q,
+                                             int lane, int64_t node, AT (&acc)[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = AT(0);
+  const int k0 = __ldg(A.off + q), w = __ldg(A.off + q + 1) - k0;
+  const VT* v0 = A.val + (size_t)k0 * 32 + lane;
+  const int ci = __ldg(A.cinfo + q);
+  if (ci < 0) {
+    const int2* u = A.uinfo + (-1 - ci);
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+      const int2 om = __ldg(u + k);   // warp-uniform: one broadcast load
+      const AT a = cvt<AT>(__ldcs(v0 + (size_t)k * 32));
+      if (((unsigned)om.y >> lane) & 1u) {
+        AT xv[NV];
+        iso_gather<NV, XT, AT>(x, node + om.x, xv);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] += a * xv[v];
+      }
+    }
+    return;
+  }
+  const int* c0 = A.col + (size_t)k0 * 32 + lane;
+#pragma unroll 4
+  for (int k = 0; k < w; ++k) {
+    const int j = __ldcs(c0 + (size_t)k * 32);
+    const AT a = cvt<AT>(__ldcs(v0 + (size_t)k * 32));
+    if (j >= 0) {
+      AT xv[NV];
+      iso_gather<NV, XT, AT>(x, j, xv);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += a * xv[v];
+    }
+  }
+}
+
+// MODE SET / RESID / ADD on S in slices, one warp per slice.
+template <int NV, int MODE, class VT, class XT, class YT, class AT>
+__global__ void __launch_bounds__(256, 4) k_iso_sell_spmv(DevSell<VT> A, const XT* __restrict__ x,
+                                                       const YT* __restrict__ f,
+                                                       YT* __restrict__ y) {
+  const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (q >= A.nslices) return;   // warp-uniform
+  const int lane = threadIdx.x & 31;
+  const int64_t node = sell_node(A, q, lane);
+  AT acc[NV];
+  iso_sell_row<NV, VT, XT, AT>(A, x, (int)q, lane, node < 0 ? 0 : node, acc);
+  if (node < 0) return;
+  iso_store<NV, MODE, XT, YT, AT>(node, acc, f, y);
+}
+
+// xo = x + m .* (f - (S (x) I) x) on S in slices; OT: the output's type
+// (the last level-0 sweep of a mixed form writes the FP64 output).
+template <int NV, class VT, class XT, class AT, class OT = XT>
+__global__ void __launch_bounds__(256, 4) k_iso_sell_relax(DevSell<VT> A, const VT* __restrict__ M,
+                                                        const XT* __restrict__ f,
+                                                        const XT* __restrict__ x,
+                                                        OT* __restrict__ xo) {
+  const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (q >= A.nslices) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t node = sell_node(A, q, lane);
+  AT acc[NV];
+  iso_sell_row<NV, VT, XT, AT>(A, x, (int)q, lane, node < 0 ? 0 : node, acc);
+  if (node < 0) return;
+  const AT mi = cvt<AT>(M[node]);
+  const size_t o = (size_t)node * NV;
+  AT fv[NV], xv[NV];
+  load_run<NV, XT, AT, false>(f + o, fv);
+  load_run<NV, XT, AT, false>(x + o, xv);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) xo[o + v] = (OT)(XT)(xv[v] + mi * (fv[v] - acc[v]));
+}
+
+// Zero-guess pre-smoothing step fused with the residual (FP64 forms):
+// x = m .* f and r = f - ((S diag(m)) (x) I) f, with S diag(m) stored in
+// the level's slices.
+template <int NV, class VT, class XT, class AT>
+__global__ void __launch_bounds__(256, 4) k_iso_sell_presmooth(DevSell<VT> AM,
+                                                            const VT* __restrict__ M,
+                                                            const XT* __restrict__ f,
+                                                            XT* __restrict__ x,
+                                                            XT* __restrict__ r) {
+  const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (q >= AM.nslices) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t node = sell_node(AM, q, lane);
+  AT acc[NV];
+  iso_sell_row<NV, VT, XT, AT>(AM, f, (int)q, lane, node < 0 ? 0 : node, acc);
+  if (node < 0) return;
+  const AT mi = cvt<AT>(M[node]);
+  const size_t o = (size_t)node * NV;
+  AT fv[NV];
+  load_run<NV, XT, AT, false>(f + o, fv);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    x[o + v] = (XT)(mi * fv[v]);
+    r[o + v] = (XT)(fv[v] - acc[v]);
+  }
+}
+
+// x = m .* f per node (the zero-guess smoothing step; diag(m) (x) I is
+// symmetric, so the transposed cycle uses it as well).
+template <int NV, class VT, class XT, class AT>
+__global__ void k_iso_mapply(int64_t n, const VT* __restrict__ M, const XT* __restrict__ f,
+                             XT* __restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = (XT)(cvt<AT>(M[i / NV]) * cvt<AT>(f[i]));
+}
+
+// The mixed forms' finest level with the FP64 -> FP32 boundary folded in:
+// fin = (XT) r (round to nearest even) and x = m .* fin.
+template <int NV, class VT, class XT, class AT>
+__global__ void k_iso_cast_mapply(int64_t n, const VT* __restrict__ M, const double* __restrict__ r,
+                                  XT* __restrict__ fin, XT* __restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const XT ri = (XT)r[i];
+    fin[i] = ri;
+    x[i] = (XT)(cvt<AT>(M[i / NV]) * cvt<AT>(ri));
+  }
+}
+
+}  // namespace gbs

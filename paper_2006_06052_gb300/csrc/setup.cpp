@@ -554,6 +554,63 @@ HCsr to_scalar_csr(const HBsr& A) {
 }
 
 namespace {
+bool same_bits(double a, double b) {
+  uint64_t x, y;
+  std::memcpy(&x, &a, 8);
+  std::memcpy(&y, &b, 8);
+  return x == y;
+}
+// One B x B row-major block: zero off the diagonal, equal diagonal.
+bool iso_block(const double* v, int B) {
+  for (int a = 0; a < B; ++a)
+    for (int c = 0; c < B; ++c) {
+      const double e = v[a * B + c];
+      if (a == c ? !same_bits(e, v[0]) : e != 0.0) return false;
+    }
+  return true;
+}
+}  // namespace
+
+bool is_iso(const HBsr& A) {
+  if (A.br != A.bc || A.br < 2) return false;
+  const int B = A.br, bs = B * B;
+  for (size_t k = 0; k < A.col.size(); ++k)
+    if (!iso_block(&A.val[k * bs], B)) return false;
+  return true;
+}
+
+bool is_iso_blocks(const std::vector<double>& M, int B) {
+  if (B < 2 || M.size() % ((size_t)B * B) != 0) return false;
+  for (size_t k = 0; k < M.size(); k += (size_t)B * B)
+    if (!iso_block(&M[k], B)) return false;
+  return true;
+}
+
+HCsr iso_scalar(const HBsr& A) {
+  HCsr C;
+  C.n = A.nbr;
+  C.ncols = A.nbc;
+  C.ptr.assign(C.n + 1, 0);
+  const int bs = A.bsz();
+  for (int i = 0; i < A.nbr; ++i) {
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      const double v = A.val[(size_t)k * bs];
+      if (v == 0.0) continue;
+      C.col.push_back(A.col[k]);
+      C.val.push_back(v);
+    }
+    C.ptr[i + 1] = (int32_t)C.col.size();
+  }
+  return C;
+}
+
+std::vector<double> iso_diag(const std::vector<double>& M, int B) {
+  std::vector<double> m(M.size() / ((size_t)B * B));
+  for (size_t i = 0; i < m.size(); ++i) m[i] = M[i * B * B];
+  return m;
+}
+
+namespace {
 // Layout of each slice of the sliced form: its width, and for a uniform
 // slice the sorted union of its rows' column offsets (col - row).  A slice
 // is uniform when that union is at most an eighth wider than its longest

@@ -87,6 +87,17 @@ HBsr scale_columns(const HBsr& A, const std::vector<double>& M);
 // row); fill = nonzeros / stored block values.
 HCsr to_scalar_csr(const HBsr& A);
 
+// Blocks that are scalar multiples of the identity.  is_iso: A has square
+// B x B blocks (B >= 2), every stored block has zero off-diagonal entries
+// and B bitwise-equal diagonal entries, so A = S (x) I_B.  iso_scalar: S as
+// scalar CSR of its nonzeros (one entry per nonzero block, columns sorted).
+// is_iso_blocks / iso_diag: the same test and the per-node value for a
+// block-diagonal smoother (n * B * B values).
+bool is_iso(const HBsr& A);
+bool is_iso_blocks(const std::vector<double>& M, int B);
+HCsr iso_scalar(const HBsr& A);
+std::vector<double> iso_diag(const std::vector<double>& M, int B);
+
 // Saad's dual-threshold ILUT (Section 4's velocity smoother), row by row
 // in natural order: eliminate the row's lower entries in increasing
 // column order (fill included), dropping an entry below tau * ||a_i||_2

@@ -225,5 +225,5 @@ def test_params_layout_matches_the_header():
     p = gb.params_default()
     assert (p.idr_s, p.idr_seed) == (5, 0)
     assert (p.ilut_p, p.ilut_tau, p.ilut_sweeps, p.ilut_omega) == (2.0, 1e-2, 2, 1.0)
-    assert (p.gmres_reorth, p.wait_log2) == (0, 31)
+    assert (p.gmres_reorth, p.wait_log2, p.iso_blocks) == (0, 31, 1)
     assert (p.relax, p.relax_p, p.level_format, p.schur_p, p.schur_order) == (0, 0, 0, 0, 0)

@@ -247,23 +247,32 @@ def _import_schur(s, pc, **kw):
                            pc.M_S.reshape(-1) if pc.M_S is not None else None, p)
 
 
+@pytest.mark.parametrize("iso", ["1", "0"])
 @pytest.mark.parametrize("fmt", ["0", "1", "2", "3", "3o"])
 @pytest.mark.parametrize("variant", [("full", "amg"), ("lower", "amg"), ("full", "spai0"),
                                      ("lower", "jacobi")])
-def test_schur_apply_on_imported_oracle_hierarchy(variant, fmt, monkeypatch):
+def test_schur_apply_on_imported_oracle_hierarchy(variant, fmt, iso, monkeypatch):
     """Eq. SchurPC (Section 4) on the oracle's own velocity and pressure
     hierarchies: the gather, the coupling kernels (r_p - D u, r_u - G p and
     their transposes through the transpose map), the inner V-cycles and
     the scatter match the oracle to 1e-12, forward and transposed, in every
-    level format (3o: slices with sorted nodes wherever rows are irregular)."""
+    level format (3o: slices with sorted nodes wherever rows are irregular).
+    The oracle's velocity levels are S (x) I_3 exactly (a scalar viscosity
+    couples u, v, w identically), so with iso = 1 they run as one scalar
+    operator on three interleaved components (except under format 1, every
+    level in block form); iso = 0 runs the per-component layouts."""
     monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt[0])
     monkeypatch.setenv("GBS_SELL_SORT", "1" if fmt.endswith("o") else "0")
+    monkeypatch.setenv("GBS_ISO", iso)
     order, pressure = variant
     s = si.make_system("c3", N=9)
     K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
     po = amg.AmgParams(coarse_enough=60)
     pc = schur.build(K, 3, po, po, order=order, pressure=pressure)
     H = _import_schur(s, pc)
+    want_iso = iso == "1" and fmt[0] != "1"
+    for l in range(len(pc.HA.levels)):
+        assert gb.level_iso(H, 0, l) == want_iso, l
     rng = np.random.default_rng(21)
     for tr in (False, True):
         r = rng.standard_normal(K.shape[0])
@@ -329,12 +338,15 @@ def test_mixed_vcycle_matches_oracle_on_cast_hierarchy(precision, fmt, monkeypat
             assert rel_inf(z, z64) > 10 * rel_inf(z, ref)
 
 
-@pytest.mark.parametrize("fmt", ["0", "3"])
+@pytest.mark.parametrize("iso", ["1", "0"])
+@pytest.mark.parametrize("fmt", ["0", "2", "3"])
 @pytest.mark.parametrize("precision", [gb.GBS_FP32, gb.GBS_BF16])
-def test_mixed_schur_matches_oracle_on_cast_hierarchy(precision, fmt, monkeypatch):
+def test_mixed_schur_matches_oracle_on_cast_hierarchy(precision, fmt, iso, monkeypatch):
     """The Schur preconditioner in the mixed forms against the oracle on
-    the cast values (velocity and pressure hierarchies, G and D), 1e-5."""
+    the cast values (velocity and pressure hierarchies, G and D), 1e-5,
+    with the velocity levels as S (x) I_3 (iso = 1) or per component."""
     monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
+    monkeypatch.setenv("GBS_ISO", iso)
     s = si.make_system("c3", N=10)
     K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
     po = amg.AmgParams(coarse_enough=60)
