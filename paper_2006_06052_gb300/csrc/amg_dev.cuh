@@ -199,6 +199,10 @@ inline bool use_fused(const HLevel& h, const PrecondOptions& o) {
   if (const char* e = std::getenv("GBS_FUSE")) return e[0] != '0';
   return true;
 }
+inline bool fuse_enabled() {
+  const char* e = std::getenv("GBS_FUSE");
+  return !(e && e[0] == '0');
+}
 
 // Per-level format choice: a level whose stored blocks are at most half
 // nonzero is kept as scalar CSR of its nonzeros (fewer bytes and, on the
@@ -499,14 +503,40 @@ void mapply(int B, int nbr, const VT* M, const XT* f, XT* x, cudaStream_t s) {
 }
 
 // ---- levels stored as S (x) I_B (iso.cuh): NV = B interleaved components
+// Lanes per row of S in the iso products: the scalar split by row length
+// (csr_split), widened on small levels until they have LANES_TARGET lanes
+// while every lane keeps at least four entries, up to a warp a row; a CTA
+// of 256 threads a row (G = 256) when even a warp a row leaves a level of
+// long rows with a quarter of that.  Measured (C3 velocity, 8 lanes a row):
+// the 42-row level-3 restriction, 481 entries a row, took 24 us in BF16
+// and 49 us in FP64; its 1108-row level-2 counterpart 29 and 48 us.
+template <class VT>
+void set_iso_lanes(DevCsr<VT>& d, int64_t rows, int64_t nnz) {
+  const double avg = rows ? (double)nnz / rows : 0.0;
+  int S = csr_split(rows, nnz);
+  while (S < 32 && rows * S < LANES_TARGET && avg >= 4.0 * S) S *= 2;
+  d.S = S;
+  d.G = S == 32 && rows * 32 < LANES_TARGET / 4 && avg >= 128.0 ? 256 : 0;
+  if (const char* e = std::getenv("GBS_ISO_SPLIT")) {   // tuning override: 1 .. 32, 256
+    const int v = std::atoi(e);
+    if (v == 256) { d.S = 32; d.G = 256; }
+    else if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32) { d.S = v; d.G = 0; }
+  }
+}
 template <int NV, int MODE, class VT, class XT, class YT, class AT>
 void iso_csr_spmv_nv(const DevCsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
+  if (A.G == 256) {
+    k_iso_csr_spmv_cta<NV, 256, MODE, VT, XT, YT, AT><<<A.n, 256, 0, s>>>(A, x, f, y);
+    return;
+  }
 #define GBS_ISO(SS) \
   k_iso_csr_spmv<NV, SS, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<1, SS>(A.n)), 256, 0, s>>>(A, x, f, y)
   switch (A.S) {
     case 2: GBS_ISO(2); break;
     case 4: GBS_ISO(4); break;
     case 8: GBS_ISO(8); break;
+    case 16: GBS_ISO(16); break;
+    case 32: GBS_ISO(32); break;
     default: GBS_ISO(1);
   }
 #undef GBS_ISO
@@ -541,12 +571,18 @@ void iso_relax_nv(const DevCsr<VT>& Ac, const DevSell<VT>& As, bool sl, const VT
         <<<grid_for((int64_t)As.nslices * 32), 256, 0, s>>>(As, M, f, x, xo);
     return;
   }
+  if (Ac.G == 256) {
+    k_iso_csr_relax_cta<NV, 256, VT, XT, AT, OT><<<Ac.n, 256, 0, s>>>(Ac, M, f, x, xo);
+    return;
+  }
 #define GBS_ISO(SS) \
   k_iso_csr_relax<NV, SS, VT, XT, AT, OT><<<grid_for(row_threads_s<1, SS>(Ac.n)), 256, 0, s>>>(Ac, M, f, x, xo)
   switch (Ac.S) {
     case 2: GBS_ISO(2); break;
     case 4: GBS_ISO(4); break;
     case 8: GBS_ISO(8); break;
+    case 16: GBS_ISO(16); break;
+    case 32: GBS_ISO(32); break;
     default: GBS_ISO(1);
   }
 #undef GBS_ISO
@@ -560,6 +596,20 @@ void iso_relax(int NV, const DevCsr<VT>& Ac, const DevSell<VT>& As, bool sl, con
     case 2: iso_relax_nv<2, VT, XT, AT, OT>(Ac, As, sl, M, f, x, xo, s); break;
     case 3: iso_relax_nv<3, VT, XT, AT, OT>(Ac, As, sl, M, f, x, xo, s); break;
     case 4: iso_relax_nv<4, VT, XT, AT, OT>(Ac, As, sl, M, f, x, xo, s); break;
+  }
+  GBS_LAUNCH_CHECK();
+}
+// Mixed forms: the same step with x = m .* f formed in the gather
+// (k_iso_sell_presmooth_otf; A holds S itself).
+template <class VT, class XT, class AT>
+void iso_presmooth_otf(int NV, const DevSell<VT>& A, const VT* M, const XT* f, XT* x, XT* r,
+                       cudaStream_t s) {
+  if (A.n == 0) return;
+  const unsigned g = grid_for((int64_t)A.nslices * 32);
+  switch (NV) {
+    case 2: k_iso_sell_presmooth_otf<2, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, r); break;
+    case 3: k_iso_sell_presmooth_otf<3, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, r); break;
+    case 4: k_iso_sell_presmooth_otf<4, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, r); break;
   }
   GBS_LAUNCH_CHECK();
 }
@@ -578,6 +628,7 @@ void iso_presmooth(int NV, const DevSell<VT>& AM, const VT* M, const XT* f, XT* 
 template <class VT, class XT, class AT>
 void iso_mapply(int NV, int64_t n, const VT* M, const XT* f, XT* x, cudaStream_t s) {
   if (n == 0) return;
+  n /= NV;   // nodes
   const unsigned g = grid_for(n);
   switch (NV) {
     case 2: k_iso_mapply<2, VT, XT, AT><<<g, 256, 0, s>>>(n, M, f, x); break;
@@ -590,6 +641,7 @@ template <class VT, class XT, class AT>
 void iso_cast_mapply(int NV, int64_t n, const VT* M, const double* r64, XT* fin, XT* x,
                      cudaStream_t s) {
   if (n == 0) return;
+  n /= NV;   // nodes
   const unsigned g = grid_for(n);
   switch (NV) {
     case 2: k_iso_cast_mapply<2, VT, XT, AT><<<g, 256, 0, s>>>(n, M, r64, fin, x); break;
@@ -822,6 +874,7 @@ struct DevAmg {
         GBS_CUDA(cudaStreamSynchronize(s));  // S's host arrays die here
       } else {
         dc = upload_csr<VT>(ar, c, s, keep);
+        set_iso_lanes(dc, c.n, nnz);
       }
     };
     const HCsr Sa = iso_scalar(h.A);
@@ -829,12 +882,16 @@ struct DevAmg {
     scalar(iso_scalar(h.P), L.Pc, L.Ps, L.p_sell, L.nnz_P, L.slots_P, L.sl_P, L.xsl_P);
     scalar(iso_scalar(h.R), L.Rc, L.Rs, L.r_sell, L.nnz_R, L.slots_R, L.sl_R, L.xsl_R);
     if (o.tmaps) {
-      L.AcT = upload_csr<VT>(ar, transpose(Sa), s, keep);
+      const HCsr St = transpose(Sa);
+      L.AcT = upload_csr<VT>(ar, St, s, keep);
+      set_iso_lanes(L.AcT, St.n, (int64_t)St.col.size());
       GBS_CUDA(cudaStreamSynchronize(s));
     }
     keep.push_back(cast_vec<VT>(iso_diag(h.M, B)));
     L.M = ar.upload(keep.back().data(), keep.back().size(), s);
-    if (use_fused<AT>(h, o) && L.a_sell) {
+    if (sizeof(AT) < 8 && o.npre == 1 && L.a_sell && fuse_enabled()) {
+      L.fused = 3;   // mixed forms: x = m .* f formed in the residual's gather
+    } else if (use_fused<AT>(h, o) && L.a_sell) {
       const HCsr c = iso_scalar(scale_columns(h.A, h.M));
       const int how = use_sell(c, 1, o.level_format);
       if (how) {
@@ -925,7 +982,8 @@ struct DevAmg {
   // x = M f and r = f - A x (zero-guess pre-smoothing + residual, fused).
   void presmooth_resid(Lev& L, const ST* f, ST* x, ST* r, cudaStream_t s) {
     if (L.iso) {
-      iso_presmooth<VT, ST, AT>(B, L.AMs, L.M, f, x, r, s);
+      if (L.fused == 3) iso_presmooth_otf<VT, ST, AT>(B, L.As, L.M, f, x, r, s);
+      else iso_presmooth<VT, ST, AT>(B, L.AMs, L.M, f, x, r, s);
       return;
     }
     if (L.fused == 2) {
@@ -984,7 +1042,7 @@ struct DevAmg {
         const ST* z = ilu_apply<TR>(L, f, s);
         k_vaxpy<ST><<<grid_for(L.n), 256, 0, s>>>(L.n, (const ST*)nullptr, (ST)ilu_omega, z, x);
         GBS_LAUNCH_CHECK();
-      } else if (L.fused && !TR && pre == 1) {
+      } else if (L.fused && !TR && pre == 1 && !(L.fused == 3 && r64)) {
         presmooth_resid(L, f, x, L.r, s);   // x = M f and r = f - A x in one pass
         have_r = true;
       } else if (r64) {
@@ -1102,10 +1160,11 @@ struct DevAmg {
         b += Abytes + Mbytes + 3 * L.n * sx;                     // relax (A, M, f, x, out)
       }
       if (L.fused) {
-        // the fused pass (A M, f gathered, M, x and r written) replaces
-        // mapply and the residual
+        // the fused pass (A M -- or A with M gathered beside f -- f
+        // gathered, M, x and r written) replaces mapply and the residual
         const double AMbytes = L.fused == 2
             ? L.slots_AM * (B * B * sv + 4) + 4.0 * L.AMb.nslices * (32 / B + 1)
+            : L.fused == 3 ? Abytes
             : sliced(L.slots_AM, L.xsl_AM, true, L.sl_AM);
         b -= (Mbytes + 2 * L.n * sx) + (Abytes + 3 * L.n * sx);
         b += AMbytes + Mbytes + 3 * L.n * sx;
@@ -1169,13 +1228,15 @@ struct AmgPrecond final : DevPrecond {
 
 // ------------------------------------------------------------- Schur kernels
 // fu[i*NV + c] = r[i*(NV+1) + c]
+// One thread a node: its NV + 1 interleaved FP64 entries load as one run.
 template <int NV, class ST>
 __global__ void k_gather_u(int nn, const double* __restrict__ r, ST* __restrict__ fu) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nn * NV;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = t / NV;
-    int c = (int)(t - i * NV);
-    fu[t] = (ST)r[i * (NV + 1) + c];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v[NV + 1];
+    load_run<NV + 1, double, double, true>(r + i * (NV + 1), v);
+#pragma unroll
+    for (int c = 0; c < NV; ++c) fu[i * NV + c] = (ST)v[c];
   }
 }
 // The couplings as scalar CSR of their nonzeros (on the FD stencil one
@@ -1221,11 +1282,20 @@ __global__ void k_diag_apply(int nn, const VT* __restrict__ m, const ST* __restr
 template <int NV, class ST>
 __global__ void k_scatter_z(int nn, const ST* __restrict__ u, const ST* __restrict__ p,
                             double* __restrict__ z) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nn * (NV + 1);
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = t / (NV + 1);
-    int c = (int)(t - i * (NV + 1));
-    z[t] = c < NV ? (double)u[i * NV + c] : (double)p[i];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v[NV + 1];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) v[c] = (double)u[i * NV + c];
+    v[NV] = (double)p[i];
+    if constexpr ((NV + 1) % 2 == 0) {   // 16-byte stores of the node's run
+#pragma unroll
+      for (int c = 0; c < NV + 1; c += 2)
+        *reinterpret_cast<double2*>(z + i * (NV + 1) + c) = make_double2(v[c], v[c + 1]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NV + 1; ++c) z[i * (NV + 1) + c] = v[c];
+    }
   }
 }
 
@@ -1295,7 +1365,7 @@ struct SchurPrecond final : DevPrecond {
   void run(const double* r, double* z, bool tr, cudaStream_t s) {
     const unsigned g = grid_for((int64_t)nn * NV);
     const unsigned gn = grid_for(nn);
-    k_gather_u<NV, ST><<<g, 256, 0, s>>>(nn, r, fu);
+    k_gather_u<NV, ST><<<gn, 256, 0, s>>>(nn, r, fu);
     GBS_LAUNCH_CHECK();
     const ST* uout = u;
     if (order == 1 && tr) {
@@ -1320,7 +1390,7 @@ struct SchurPrecond final : DevPrecond {
         A.vcycle(fu2, u, tr, s);
       }
     }
-    k_scatter_z<NV, ST><<<grid_for((int64_t)nn * (NV + 1)), 256, 0, s>>>(nn, uout, p, z);
+    k_scatter_z<NV, ST><<<gn, 256, 0, s>>>(nn, uout, p, z);
     GBS_LAUNCH_CHECK();
   }
 

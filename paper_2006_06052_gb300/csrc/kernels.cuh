@@ -305,6 +305,10 @@ inline int choose_group(int64_t nbr, int64_t nnzb) {
     // few very long rows (a CTA per row measured 3x slower than a warp per
     // row on the 2017-row level 2 of C2)
     if (nbr <= 1024 && avg >= 128.0) return 256;
+    // a warp per scalar row for a small level of long rows, where eight
+    // lanes a row (the widest split) leave the GPU mostly idle (C3's
+    // 1579-row level-3 pressure operator, 325 entries a row)
+    if (B == 1 && nbr * 8 < LANES_TARGET / 4 && avg >= 64.0) return 32;
     return 0;
   }
   // a CTA per row when a warp per row leaves the GPU mostly idle and each

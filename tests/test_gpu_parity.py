@@ -248,7 +248,7 @@ def _import_schur(s, pc, **kw):
 
 
 @pytest.mark.parametrize("iso", ["1", "0"])
-@pytest.mark.parametrize("fmt", ["0", "1", "2", "3", "3o"])
+@pytest.mark.parametrize("fmt", ["0", "0f", "1", "2", "3", "3o"])
 @pytest.mark.parametrize("variant", [("full", "amg"), ("lower", "amg"), ("full", "spai0"),
                                      ("lower", "jacobi")])
 def test_schur_apply_on_imported_oracle_hierarchy(variant, fmt, iso, monkeypatch):
@@ -256,13 +256,15 @@ def test_schur_apply_on_imported_oracle_hierarchy(variant, fmt, iso, monkeypatch
     hierarchies: the gather, the coupling kernels (r_p - D u, r_u - G p and
     their transposes through the transpose map), the inner V-cycles and
     the scatter match the oracle to 1e-12, forward and transposed, in every
-    level format (3o: slices with sorted nodes wherever rows are irregular).
+    level format (3o: slices with sorted nodes wherever rows are irregular;
+    0f: without the fused zero-guess smoothing step).
     The oracle's velocity levels are S (x) I_3 exactly (a scalar viscosity
     couples u, v, w identically), so with iso = 1 they run as one scalar
     operator on three interleaved components (except under format 1, every
     level in block form); iso = 0 runs the per-component layouts."""
     monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt[0])
     monkeypatch.setenv("GBS_SELL_SORT", "1" if fmt.endswith("o") else "0")
+    monkeypatch.setenv("GBS_FUSE", "0" if fmt.endswith("f") else "1")
     monkeypatch.setenv("GBS_ISO", iso)
     order, pressure = variant
     s = si.make_system("c3", N=9)
@@ -339,13 +341,16 @@ def test_mixed_vcycle_matches_oracle_on_cast_hierarchy(precision, fmt, monkeypat
 
 
 @pytest.mark.parametrize("iso", ["1", "0"])
-@pytest.mark.parametrize("fmt", ["0", "2", "3"])
+@pytest.mark.parametrize("fmt", ["0", "0f", "2", "3"])
 @pytest.mark.parametrize("precision", [gb.GBS_FP32, gb.GBS_BF16])
 def test_mixed_schur_matches_oracle_on_cast_hierarchy(precision, fmt, iso, monkeypatch):
     """The Schur preconditioner in the mixed forms against the oracle on
     the cast values (velocity and pressure hierarchies, G and D), 1e-5,
-    with the velocity levels as S (x) I_3 (iso = 1) or per component."""
-    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
+    with the velocity levels as S (x) I_3 (iso = 1) or per component; 0f
+    keeps the zero-guess smoothing step apart from the residual (fused,
+    an S (x) I_3 level forms x = m .* f in the residual's gather)."""
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt[0])
+    monkeypatch.setenv("GBS_FUSE", "0" if fmt.endswith("f") else "1")
     monkeypatch.setenv("GBS_ISO", iso)
     s = si.make_system("c3", N=10)
     K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
@@ -359,6 +364,33 @@ def test_mixed_schur_matches_oracle_on_cast_hierarchy(precision, fmt, iso, monke
         z = host(gb.apply_precond(H, dev(r), transpose=tr))
         ref = pcc.apply(round_to(r, "fp32"), transpose=tr)
         assert rel_inf(z, ref) <= 1e-5, (tr, rel_inf(z, ref))
+
+
+@pytest.mark.parametrize("split", ["1", "2", "16", "32", "256"])
+@pytest.mark.parametrize("precision", [gb.GBS_FP64, gb.GBS_BF16])
+def test_iso_lane_groups_match_oracle(precision, split, monkeypatch):
+    """Every S (x) I_3 velocity level in plain CSR, with 1 .. 32 lanes a row
+    of S or a 256-thread CTA a row (the widths small levels of long rows
+    take), forward and transposed, against the oracle's Schur application
+    on the same (for BF16: cast) hierarchy."""
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", "2")
+    monkeypatch.setenv("GBS_ISO", "1")
+    monkeypatch.setenv("GBS_ISO_SPLIT", split)
+    s = si.make_system("c3", N=10)
+    K = bsr.from_arrays(s.indptr, s.indices, s.data, 4)
+    po = amg.AmgParams(coarse_enough=60)
+    pc = schur.build(K, 3, po, po)
+    H = _import_schur(s, pc, precision=precision)
+    assert all(gb.level_iso(H, 0, l) for l in range(len(pc.HA.levels)))
+    ref_pc = pc if precision == gb.GBS_FP64 else schur.cast_values(pc, FMT[precision])
+    rng = np.random.default_rng(43)
+    for tr in (False, True):
+        r = rng.standard_normal(K.shape[0])
+        z = host(gb.apply_precond(H, dev(r), transpose=tr))
+        if precision == gb.GBS_FP64:
+            assert rel_inf(z, ref_pc.apply(r, transpose=tr)) <= 1e-12, tr
+        else:
+            assert rel_inf(z, ref_pc.apply(round_to(r, "fp32"), transpose=tr)) <= 1e-5, tr
 
 
 # ----------------------------------------------------------------- solves
