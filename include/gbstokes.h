@@ -141,12 +141,14 @@ typedef struct {
                              of A_l, P_l, R_l and the smoother -- is a scalar
                              multiple of the identity (checked exactly; the
                              velocity hierarchy of a scalar-viscosity Stokes
-                             system is) is stored as the scalar matrix S with
+                             system is, and every scalar level trivially) is
+                             stored as the scalar matrix S with
                              A_l = S (x) I_B, one value and one column a block,
                              and each product applies S to the B interleaved
-                             components at once (unless level_format is 1);
-                             0: such levels follow level_format like any
-                             other */
+                             components at once, in 32-node slices or with
+                             lane groups sized to the level (unless
+                             level_format is 1); 0: such levels follow
+                             level_format like any other */
 } gbs_params;
 
 typedef struct {

@@ -549,6 +549,7 @@ void iso_spmv(int NV, const DevCsr<VT>& Ac, const DevSell<VT>& As, bool sl, cons
     if (As.n == 0) return;
     const unsigned g = grid_for((int64_t)As.nslices * 32);
     switch (NV) {
+      case 1: k_iso_sell_spmv<1, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(As, x, f, y); break;
       case 2: k_iso_sell_spmv<2, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(As, x, f, y); break;
       case 3: k_iso_sell_spmv<3, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(As, x, f, y); break;
       case 4: k_iso_sell_spmv<4, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(As, x, f, y); break;
@@ -556,6 +557,7 @@ void iso_spmv(int NV, const DevCsr<VT>& Ac, const DevSell<VT>& As, bool sl, cons
   } else {
     if (Ac.n == 0) return;
     switch (NV) {
+      case 1: iso_csr_spmv_nv<1, MODE, VT, XT, YT, AT>(Ac, x, f, y, s); break;
       case 2: iso_csr_spmv_nv<2, MODE, VT, XT, YT, AT>(Ac, x, f, y, s); break;
       case 3: iso_csr_spmv_nv<3, MODE, VT, XT, YT, AT>(Ac, x, f, y, s); break;
       case 4: iso_csr_spmv_nv<4, MODE, VT, XT, YT, AT>(Ac, x, f, y, s); break;
@@ -593,6 +595,7 @@ void iso_relax(int NV, const DevCsr<VT>& Ac, const DevSell<VT>& As, bool sl, con
                const XT* f, const XT* x, OT* xo, cudaStream_t s) {
   if (sl ? As.n == 0 : Ac.n == 0) return;
   switch (NV) {
+    case 1: iso_relax_nv<1, VT, XT, AT, OT>(Ac, As, sl, M, f, x, xo, s); break;
     case 2: iso_relax_nv<2, VT, XT, AT, OT>(Ac, As, sl, M, f, x, xo, s); break;
     case 3: iso_relax_nv<3, VT, XT, AT, OT>(Ac, As, sl, M, f, x, xo, s); break;
     case 4: iso_relax_nv<4, VT, XT, AT, OT>(Ac, As, sl, M, f, x, xo, s); break;
@@ -607,6 +610,7 @@ void iso_presmooth_otf(int NV, const DevSell<VT>& A, const VT* M, const XT* f, X
   if (A.n == 0) return;
   const unsigned g = grid_for((int64_t)A.nslices * 32);
   switch (NV) {
+    case 1: k_iso_sell_presmooth_otf<1, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, r); break;
     case 2: k_iso_sell_presmooth_otf<2, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, r); break;
     case 3: k_iso_sell_presmooth_otf<3, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, r); break;
     case 4: k_iso_sell_presmooth_otf<4, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, r); break;
@@ -619,6 +623,7 @@ void iso_presmooth(int NV, const DevSell<VT>& AM, const VT* M, const XT* f, XT* 
   if (AM.n == 0) return;
   const unsigned g = grid_for((int64_t)AM.nslices * 32);
   switch (NV) {
+    case 1: k_iso_sell_presmooth<1, VT, XT, AT><<<g, 256, 0, s>>>(AM, M, f, x, r); break;
     case 2: k_iso_sell_presmooth<2, VT, XT, AT><<<g, 256, 0, s>>>(AM, M, f, x, r); break;
     case 3: k_iso_sell_presmooth<3, VT, XT, AT><<<g, 256, 0, s>>>(AM, M, f, x, r); break;
     case 4: k_iso_sell_presmooth<4, VT, XT, AT><<<g, 256, 0, s>>>(AM, M, f, x, r); break;
@@ -631,6 +636,7 @@ void iso_mapply(int NV, int64_t n, const VT* M, const XT* f, XT* x, cudaStream_t
   n /= NV;   // nodes
   const unsigned g = grid_for(n);
   switch (NV) {
+    case 1: k_iso_mapply<1, VT, XT, AT><<<g, 256, 0, s>>>(n, M, f, x); break;
     case 2: k_iso_mapply<2, VT, XT, AT><<<g, 256, 0, s>>>(n, M, f, x); break;
     case 3: k_iso_mapply<3, VT, XT, AT><<<g, 256, 0, s>>>(n, M, f, x); break;
     case 4: k_iso_mapply<4, VT, XT, AT><<<g, 256, 0, s>>>(n, M, f, x); break;
@@ -644,6 +650,7 @@ void iso_cast_mapply(int NV, int64_t n, const VT* M, const double* r64, XT* fin,
   n /= NV;   // nodes
   const unsigned g = grid_for(n);
   switch (NV) {
+    case 1: k_iso_cast_mapply<1, VT, XT, AT><<<g, 256, 0, s>>>(n, M, r64, fin, x); break;
     case 2: k_iso_cast_mapply<2, VT, XT, AT><<<g, 256, 0, s>>>(n, M, r64, fin, x); break;
     case 3: k_iso_cast_mapply<3, VT, XT, AT><<<g, 256, 0, s>>>(n, M, r64, fin, x); break;
     case 4: k_iso_cast_mapply<4, VT, XT, AT><<<g, 256, 0, s>>>(n, M, r64, fin, x); break;
@@ -848,8 +855,9 @@ struct DevAmg {
     bool on = o.iso;
     if (const char* e = std::getenv("GBS_ISO")) on = e[0] != '0';
     if (level_format_of(o.level_format) == 1) on = false;
-    return on && B > 1 && h.ilu.d.empty() && !h.M.empty() && is_iso(h.A) && is_iso(h.P) &&
-           is_iso(h.R) && is_iso_blocks(h.M, B);
+    if (!on || !h.ilu.d.empty() || h.M.empty()) return false;
+    // a scalar level is S (x) I_1: one lane a row, in slices or wide CSR
+    return B == 1 || (is_iso(h.A) && is_iso(h.P) && is_iso(h.R) && is_iso_blocks(h.M, B));
   }
   void build_iso(const HLevel& h, const PrecondOptions& o, Lev& L, cudaStream_t s,
                  std::vector<std::vector<VT>>& keep) {
