@@ -296,7 +296,7 @@ template <int B, int MODE, class VT, class XT, class YT, class AT>
 void sell_spmv_g(const DevSell<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
   const int64_t groups = (int64_t)A.nslices / B;
   if (sell_direct<VT, AT>(A))
-    k_sell_spmv_direct_g<B, MODE, VT, XT, YT, AT><<<grid_for(groups * 32), 256, 0, s>>>(A, x, f, y);
+    ::gbs::launch_k(k_sell_spmv_direct_g<B, MODE, VT, XT, YT, AT>, grid_for(groups * 32), 256, 0, s, A, x, f, y);
   else
     launch_sell(k_sell_spmv_g<B, MODE, VT, XT, YT, AT>, sell_smem_bytes<VT>(),
                 (groups + SELL_WARPS - 1) / SELL_WARPS, s, A, x, f, y);
@@ -311,8 +311,8 @@ void sell_spmv(const DevSell<VT>& A, const XT* x, const YT* f, YT* y, cudaStream
       default: sell_spmv_g<4, MODE, VT, XT, YT, AT>(A, x, f, y, s); break;
     }
   } else if (sell_direct<VT, AT>(A)) {
-    k_sell_spmv_direct<MODE, VT, XT, YT, AT>
-        <<<grid_for((int64_t)A.nslices * 32), 256, 0, s>>>(A, x, f, y);
+    ::gbs::launch_k(k_sell_spmv_direct<MODE, VT, XT, YT, AT>
+        , grid_for((int64_t)A.nslices * 32), 256, 0, s, A, x, f, y);
   } else {
     launch_sell(k_sell_spmv<MODE, VT, XT, YT, AT>, sell_smem_bytes<VT>(),
                 ((int64_t)A.nslices + SELL_WARPS - 1) / SELL_WARPS, s, A, x, f, y);
@@ -324,7 +324,7 @@ void sell_relax_B(const DevSell<VT>& A, const VT* M, const XT* f, const XT* x, O
                   cudaStream_t s) {
   const int64_t groups = (int64_t)A.nslices / B;
   if (sell_direct<VT, AT>(A)) {
-    k_sell_relax_direct<B, VT, XT, AT, OT><<<grid_for(groups * 32), 256, 0, s>>>(A, M, f, x, xo);
+    ::gbs::launch_k(k_sell_relax_direct<B, VT, XT, AT, OT>, grid_for(groups * 32), 256, 0, s, A, M, f, x, xo);
   } else {
     launch_sell(k_sell_relax<B, VT, XT, AT, OT>, sell_smem_bytes<VT>(),
                 (groups + SELL_WARPS - 1) / SELL_WARPS, s, A, M, f, x, xo);
@@ -363,10 +363,10 @@ void csr_spmv(const DevCsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t
     return;
   }
   switch (A.S) {
-    case 2: k_csr_spmv<2, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<1, 2>(A.n)), 256, 0, s>>>(A, x, f, y); break;
-    case 4: k_csr_spmv<4, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<1, 4>(A.n)), 256, 0, s>>>(A, x, f, y); break;
-    case 8: k_csr_spmv<8, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<1, 8>(A.n)), 256, 0, s>>>(A, x, f, y); break;
-    default: k_csr_spmv<1, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<1, 1>(A.n)), 256, 0, s>>>(A, x, f, y);
+    case 2: ::gbs::launch_k(k_csr_spmv<2, MODE, VT, XT, YT, AT>, grid_for(row_threads_s<1, 2>(A.n)), 256, 0, s, A, x, f, y); break;
+    case 4: ::gbs::launch_k(k_csr_spmv<4, MODE, VT, XT, YT, AT>, grid_for(row_threads_s<1, 4>(A.n)), 256, 0, s, A, x, f, y); break;
+    case 8: ::gbs::launch_k(k_csr_spmv<8, MODE, VT, XT, YT, AT>, grid_for(row_threads_s<1, 8>(A.n)), 256, 0, s, A, x, f, y); break;
+    default: ::gbs::launch_k(k_csr_spmv<1, MODE, VT, XT, YT, AT>, grid_for(row_threads_s<1, 1>(A.n)), 256, 0, s, A, x, f, y);
   }
   GBS_LAUNCH_CHECK();
 }
@@ -374,14 +374,14 @@ template <int B, class VT, class XT, class AT>
 void csr_relax_B(const DevCsr<VT>& A, const VT* M, const XT* f, const XT* x, XT* xo, cudaStream_t s) {
   const int nn = A.n / B;
   switch (A.S) {
-    case 2: k_csr_relax<B, 2, VT, XT, AT><<<grid_for(row_threads_s<B, 2>(nn)), 256, 0, s>>>(A, M, f, x, xo); break;
+    case 2: ::gbs::launch_k(k_csr_relax<B, 2, VT, XT, AT>, grid_for(row_threads_s<B, 2>(nn)), 256, 0, s, A, M, f, x, xo); break;
     case 4:
-      if constexpr (B * 4 <= 32) k_csr_relax<B, 4, VT, XT, AT><<<grid_for(row_threads_s<B, 4>(nn)), 256, 0, s>>>(A, M, f, x, xo);
+      if constexpr (B * 4 <= 32) ::gbs::launch_k(k_csr_relax<B, 4, VT, XT, AT>, grid_for(row_threads_s<B, 4>(nn)), 256, 0, s, A, M, f, x, xo);
       break;
     case 8:
-      if constexpr (B * 8 <= 32) k_csr_relax<B, 8, VT, XT, AT><<<grid_for(row_threads_s<B, 8>(nn)), 256, 0, s>>>(A, M, f, x, xo);
+      if constexpr (B * 8 <= 32) ::gbs::launch_k(k_csr_relax<B, 8, VT, XT, AT>, grid_for(row_threads_s<B, 8>(nn)), 256, 0, s, A, M, f, x, xo);
       break;
-    default: k_csr_relax<B, 1, VT, XT, AT><<<grid_for(row_threads_s<B, 1>(nn)), 256, 0, s>>>(A, M, f, x, xo);
+    default: ::gbs::launch_k(k_csr_relax<B, 1, VT, XT, AT>, grid_for(row_threads_s<B, 1>(nn)), 256, 0, s, A, M, f, x, xo);
   }
 }
 template <class VT, class XT, class AT>
@@ -402,10 +402,10 @@ void bsell_spmv(int B, const DevBSell<VT>& A, const XT* x, const YT* f, YT* y, c
   if (A.nslices == 0) return;
   const unsigned g = grid_for((int64_t)A.nslices * 32);
   switch (B) {
-    case 1: k_bsell_spmv<1, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(A, x, f, y); break;
-    case 2: k_bsell_spmv<2, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(A, x, f, y); break;
-    case 3: k_bsell_spmv<3, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(A, x, f, y); break;
-    case 4: k_bsell_spmv<4, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(A, x, f, y); break;
+    case 1: ::gbs::launch_k(k_bsell_spmv<1, MODE, VT, XT, YT, AT>, g, 256, 0, s, A, x, f, y); break;
+    case 2: ::gbs::launch_k(k_bsell_spmv<2, MODE, VT, XT, YT, AT>, g, 256, 0, s, A, x, f, y); break;
+    case 3: ::gbs::launch_k(k_bsell_spmv<3, MODE, VT, XT, YT, AT>, g, 256, 0, s, A, x, f, y); break;
+    case 4: ::gbs::launch_k(k_bsell_spmv<4, MODE, VT, XT, YT, AT>, g, 256, 0, s, A, x, f, y); break;
   }
   GBS_LAUNCH_CHECK();
 }
@@ -415,10 +415,10 @@ void bsell_relax(int B, const DevBSell<VT>& A, const VT* M, const XT* f, const X
   if (A.nslices == 0) return;
   const unsigned g = grid_for((int64_t)A.nslices * 32);
   switch (B) {
-    case 1: k_bsell_relax<1, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, xo); break;
-    case 2: k_bsell_relax<2, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, xo); break;
-    case 3: k_bsell_relax<3, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, xo); break;
-    case 4: k_bsell_relax<4, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, xo); break;
+    case 1: ::gbs::launch_k(k_bsell_relax<1, VT, XT, AT>, g, 256, 0, s, A, M, f, x, xo); break;
+    case 2: ::gbs::launch_k(k_bsell_relax<2, VT, XT, AT>, g, 256, 0, s, A, M, f, x, xo); break;
+    case 3: ::gbs::launch_k(k_bsell_relax<3, VT, XT, AT>, g, 256, 0, s, A, M, f, x, xo); break;
+    case 4: ::gbs::launch_k(k_bsell_relax<4, VT, XT, AT>, g, 256, 0, s, A, M, f, x, xo); break;
   }
   GBS_LAUNCH_CHECK();
 }
@@ -429,20 +429,20 @@ void spmv_B(const DevBsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s
   if (A.nbr == 0) return;
   const int64_t nt = (int64_t)A.nbr * A.G;
   switch (A.G) {
-    case 8: k_spmv_w<B, 8, TR, MODE, VT, XT, YT, AT><<<grid_for(nt), 256, 0, s>>>(A, x, f, y); break;
-    case 16: k_spmv_w<B, 16, TR, MODE, VT, XT, YT, AT><<<grid_for(nt), 256, 0, s>>>(A, x, f, y); break;
-    case 32: k_spmv_w<B, 32, TR, MODE, VT, XT, YT, AT><<<grid_for(nt), 256, 0, s>>>(A, x, f, y); break;
-    case 256: k_spmv_w<B, 256, TR, MODE, VT, XT, YT, AT><<<grid_for(nt), 256, 0, s>>>(A, x, f, y); break;
+    case 8: ::gbs::launch_k(k_spmv_w<B, 8, TR, MODE, VT, XT, YT, AT>, grid_for(nt), 256, 0, s, A, x, f, y); break;
+    case 16: ::gbs::launch_k(k_spmv_w<B, 16, TR, MODE, VT, XT, YT, AT>, grid_for(nt), 256, 0, s, A, x, f, y); break;
+    case 32: ::gbs::launch_k(k_spmv_w<B, 32, TR, MODE, VT, XT, YT, AT>, grid_for(nt), 256, 0, s, A, x, f, y); break;
+    case 256: ::gbs::launch_k(k_spmv_w<B, 256, TR, MODE, VT, XT, YT, AT>, grid_for(nt), 256, 0, s, A, x, f, y); break;
     default:
       switch (A.S) {
-        case 2: k_spmv<B, 2, TR, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<B, 2>(A.nbr)), 256, 0, s>>>(A, x, f, y); break;
+        case 2: ::gbs::launch_k(k_spmv<B, 2, TR, MODE, VT, XT, YT, AT>, grid_for(row_threads_s<B, 2>(A.nbr)), 256, 0, s, A, x, f, y); break;
         case 4:
-          if constexpr (B * 4 <= 32) k_spmv<B, 4, TR, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<B, 4>(A.nbr)), 256, 0, s>>>(A, x, f, y);
+          if constexpr (B * 4 <= 32) ::gbs::launch_k(k_spmv<B, 4, TR, MODE, VT, XT, YT, AT>, grid_for(row_threads_s<B, 4>(A.nbr)), 256, 0, s, A, x, f, y);
           break;
         case 8:
-          if constexpr (B * 8 <= 32) k_spmv<B, 8, TR, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<B, 8>(A.nbr)), 256, 0, s>>>(A, x, f, y);
+          if constexpr (B * 8 <= 32) ::gbs::launch_k(k_spmv<B, 8, TR, MODE, VT, XT, YT, AT>, grid_for(row_threads_s<B, 8>(A.nbr)), 256, 0, s, A, x, f, y);
           break;
-        default: k_spmv<B, 1, TR, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<B, 1>(A.nbr)), 256, 0, s>>>(A, x, f, y);
+        default: ::gbs::launch_k(k_spmv<B, 1, TR, MODE, VT, XT, YT, AT>, grid_for(row_threads_s<B, 1>(A.nbr)), 256, 0, s, A, x, f, y);
       }
   }
 }
@@ -462,20 +462,20 @@ void relax(int B, const DevBsr<VT>& A, const VT* M, const XT* f, const XT* x, XT
   if (A.nbr == 0) return;
 #define GBS_RELAX(BB)                                                                            \
   switch (A.G) {                                                                                 \
-    case 8: k_relax_w<BB, 8, TR, VT, XT, AT><<<grid_for((int64_t)A.nbr * 8), 256, 0, s>>>(A, M, f, x, xo); break;   \
-    case 16: k_relax_w<BB, 16, TR, VT, XT, AT><<<grid_for((int64_t)A.nbr * 16), 256, 0, s>>>(A, M, f, x, xo); break; \
-    case 32: k_relax_w<BB, 32, TR, VT, XT, AT><<<grid_for((int64_t)A.nbr * 32), 256, 0, s>>>(A, M, f, x, xo); break; \
-    case 256: k_relax_w<BB, 256, TR, VT, XT, AT><<<grid_for((int64_t)A.nbr * 256), 256, 0, s>>>(A, M, f, x, xo); break; \
+    case 8: ::gbs::launch_k(k_relax_w<BB, 8, TR, VT, XT, AT>, grid_for((int64_t)A.nbr * 8), 256, 0, s, A, M, f, x, xo); break;   \
+    case 16: ::gbs::launch_k(k_relax_w<BB, 16, TR, VT, XT, AT>, grid_for((int64_t)A.nbr * 16), 256, 0, s, A, M, f, x, xo); break; \
+    case 32: ::gbs::launch_k(k_relax_w<BB, 32, TR, VT, XT, AT>, grid_for((int64_t)A.nbr * 32), 256, 0, s, A, M, f, x, xo); break; \
+    case 256: ::gbs::launch_k(k_relax_w<BB, 256, TR, VT, XT, AT>, grid_for((int64_t)A.nbr * 256), 256, 0, s, A, M, f, x, xo); break; \
     default:                                                                                     \
       switch (A.S) {                                                                             \
-        case 2: k_relax<BB, 2, TR, VT, XT, AT><<<grid_for(row_threads_s<BB, 2>(A.nbr)), 256, 0, s>>>(A, M, f, x, xo); break; \
+        case 2: ::gbs::launch_k(k_relax<BB, 2, TR, VT, XT, AT>, grid_for(row_threads_s<BB, 2>(A.nbr)), 256, 0, s, A, M, f, x, xo); break; \
         case 4:                                                                                  \
-          if constexpr (BB * 4 <= 32) k_relax<BB, 4, TR, VT, XT, AT><<<grid_for(row_threads_s<BB, 4>(A.nbr)), 256, 0, s>>>(A, M, f, x, xo); \
+          if constexpr (BB * 4 <= 32) ::gbs::launch_k(k_relax<BB, 4, TR, VT, XT, AT>, grid_for(row_threads_s<BB, 4>(A.nbr)), 256, 0, s, A, M, f, x, xo); \
           break;                                                                                 \
         case 8:                                                                                  \
-          if constexpr (BB * 8 <= 32) k_relax<BB, 8, TR, VT, XT, AT><<<grid_for(row_threads_s<BB, 8>(A.nbr)), 256, 0, s>>>(A, M, f, x, xo); \
+          if constexpr (BB * 8 <= 32) ::gbs::launch_k(k_relax<BB, 8, TR, VT, XT, AT>, grid_for(row_threads_s<BB, 8>(A.nbr)), 256, 0, s, A, M, f, x, xo); \
           break;                                                                                 \
-        default: k_relax<BB, 1, TR, VT, XT, AT><<<grid_for(row_threads_s<BB, 1>(A.nbr)), 256, 0, s>>>(A, M, f, x, xo); \
+        default: ::gbs::launch_k(k_relax<BB, 1, TR, VT, XT, AT>, grid_for(row_threads_s<BB, 1>(A.nbr)), 256, 0, s, A, M, f, x, xo); \
       }                                                                                          \
   }
   switch (B) {
@@ -491,7 +491,7 @@ template <bool TR, class VT, class XT, class AT>
 void mapply(int B, int nbr, const VT* M, const XT* f, XT* x, cudaStream_t s) {
   if (nbr == 0) return;
 #define GBS_MAP(BB) \
-  k_mapply<BB, TR, VT, XT, AT><<<grid_for(row_threads<BB>(nbr)), 256, 0, s>>>(nbr, M, f, x)
+  ::gbs::launch_k(k_mapply<BB, TR, VT, XT, AT>, grid_for(row_threads<BB>(nbr)), 256, 0, s, nbr, M, f, x)
   switch (B) {
     case 1: GBS_MAP(1); break;
     case 2: GBS_MAP(2); break;
@@ -526,11 +526,11 @@ void set_iso_lanes(DevCsr<VT>& d, int64_t rows, int64_t nnz) {
 template <int NV, int MODE, class VT, class XT, class YT, class AT>
 void iso_csr_spmv_nv(const DevCsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
   if (A.G == 256) {
-    k_iso_csr_spmv_cta<NV, 256, MODE, VT, XT, YT, AT><<<A.n, 256, 0, s>>>(A, x, f, y);
+    ::gbs::launch_k(k_iso_csr_spmv_cta<NV, 256, MODE, VT, XT, YT, AT>, A.n, 256, 0, s, A, x, f, y);
     return;
   }
 #define GBS_ISO(SS) \
-  k_iso_csr_spmv<NV, SS, MODE, VT, XT, YT, AT><<<grid_for(row_threads_s<1, SS>(A.n)), 256, 0, s>>>(A, x, f, y)
+  ::gbs::launch_k(k_iso_csr_spmv<NV, SS, MODE, VT, XT, YT, AT>, grid_for(row_threads_s<1, SS>(A.n)), 256, 0, s, A, x, f, y)
   switch (A.S) {
     case 2: GBS_ISO(2); break;
     case 4: GBS_ISO(4); break;
@@ -549,10 +549,10 @@ void iso_spmv(int NV, const DevCsr<VT>& Ac, const DevSell<VT>& As, bool sl, cons
     if (As.n == 0) return;
     const unsigned g = grid_for((int64_t)As.nslices * 32);
     switch (NV) {
-      case 1: k_iso_sell_spmv<1, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(As, x, f, y); break;
-      case 2: k_iso_sell_spmv<2, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(As, x, f, y); break;
-      case 3: k_iso_sell_spmv<3, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(As, x, f, y); break;
-      case 4: k_iso_sell_spmv<4, MODE, VT, XT, YT, AT><<<g, 256, 0, s>>>(As, x, f, y); break;
+      case 1: ::gbs::launch_k(k_iso_sell_spmv<1, MODE, VT, XT, YT, AT>, g, 256, 0, s, As, x, f, y); break;
+      case 2: ::gbs::launch_k(k_iso_sell_spmv<2, MODE, VT, XT, YT, AT>, g, 256, 0, s, As, x, f, y); break;
+      case 3: ::gbs::launch_k(k_iso_sell_spmv<3, MODE, VT, XT, YT, AT>, g, 256, 0, s, As, x, f, y); break;
+      case 4: ::gbs::launch_k(k_iso_sell_spmv<4, MODE, VT, XT, YT, AT>, g, 256, 0, s, As, x, f, y); break;
     }
   } else {
     if (Ac.n == 0) return;
@@ -569,16 +569,16 @@ template <int NV, class VT, class XT, class AT, class OT>
 void iso_relax_nv(const DevCsr<VT>& Ac, const DevSell<VT>& As, bool sl, const VT* M, const XT* f,
                   const XT* x, OT* xo, cudaStream_t s) {
   if (sl) {
-    k_iso_sell_relax<NV, VT, XT, AT, OT>
-        <<<grid_for((int64_t)As.nslices * 32), 256, 0, s>>>(As, M, f, x, xo);
+    ::gbs::launch_k(k_iso_sell_relax<NV, VT, XT, AT, OT>
+        , grid_for((int64_t)As.nslices * 32), 256, 0, s, As, M, f, x, xo);
     return;
   }
   if (Ac.G == 256) {
-    k_iso_csr_relax_cta<NV, 256, VT, XT, AT, OT><<<Ac.n, 256, 0, s>>>(Ac, M, f, x, xo);
+    ::gbs::launch_k(k_iso_csr_relax_cta<NV, 256, VT, XT, AT, OT>, Ac.n, 256, 0, s, Ac, M, f, x, xo);
     return;
   }
 #define GBS_ISO(SS) \
-  k_iso_csr_relax<NV, SS, VT, XT, AT, OT><<<grid_for(row_threads_s<1, SS>(Ac.n)), 256, 0, s>>>(Ac, M, f, x, xo)
+  ::gbs::launch_k(k_iso_csr_relax<NV, SS, VT, XT, AT, OT>, grid_for(row_threads_s<1, SS>(Ac.n)), 256, 0, s, Ac, M, f, x, xo)
   switch (Ac.S) {
     case 2: GBS_ISO(2); break;
     case 4: GBS_ISO(4); break;
@@ -610,10 +610,10 @@ void iso_presmooth_otf(int NV, const DevSell<VT>& A, const VT* M, const XT* f, X
   if (A.n == 0) return;
   const unsigned g = grid_for((int64_t)A.nslices * 32);
   switch (NV) {
-    case 1: k_iso_sell_presmooth_otf<1, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, r); break;
-    case 2: k_iso_sell_presmooth_otf<2, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, r); break;
-    case 3: k_iso_sell_presmooth_otf<3, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, r); break;
-    case 4: k_iso_sell_presmooth_otf<4, VT, XT, AT><<<g, 256, 0, s>>>(A, M, f, x, r); break;
+    case 1: ::gbs::launch_k(k_iso_sell_presmooth_otf<1, VT, XT, AT>, g, 256, 0, s, A, M, f, x, r); break;
+    case 2: ::gbs::launch_k(k_iso_sell_presmooth_otf<2, VT, XT, AT>, g, 256, 0, s, A, M, f, x, r); break;
+    case 3: ::gbs::launch_k(k_iso_sell_presmooth_otf<3, VT, XT, AT>, g, 256, 0, s, A, M, f, x, r); break;
+    case 4: ::gbs::launch_k(k_iso_sell_presmooth_otf<4, VT, XT, AT>, g, 256, 0, s, A, M, f, x, r); break;
   }
   GBS_LAUNCH_CHECK();
 }
@@ -623,10 +623,10 @@ void iso_presmooth(int NV, const DevSell<VT>& AM, const VT* M, const XT* f, XT* 
   if (AM.n == 0) return;
   const unsigned g = grid_for((int64_t)AM.nslices * 32);
   switch (NV) {
-    case 1: k_iso_sell_presmooth<1, VT, XT, AT><<<g, 256, 0, s>>>(AM, M, f, x, r); break;
-    case 2: k_iso_sell_presmooth<2, VT, XT, AT><<<g, 256, 0, s>>>(AM, M, f, x, r); break;
-    case 3: k_iso_sell_presmooth<3, VT, XT, AT><<<g, 256, 0, s>>>(AM, M, f, x, r); break;
-    case 4: k_iso_sell_presmooth<4, VT, XT, AT><<<g, 256, 0, s>>>(AM, M, f, x, r); break;
+    case 1: ::gbs::launch_k(k_iso_sell_presmooth<1, VT, XT, AT>, g, 256, 0, s, AM, M, f, x, r); break;
+    case 2: ::gbs::launch_k(k_iso_sell_presmooth<2, VT, XT, AT>, g, 256, 0, s, AM, M, f, x, r); break;
+    case 3: ::gbs::launch_k(k_iso_sell_presmooth<3, VT, XT, AT>, g, 256, 0, s, AM, M, f, x, r); break;
+    case 4: ::gbs::launch_k(k_iso_sell_presmooth<4, VT, XT, AT>, g, 256, 0, s, AM, M, f, x, r); break;
   }
   GBS_LAUNCH_CHECK();
 }
@@ -636,10 +636,10 @@ void iso_mapply(int NV, int64_t n, const VT* M, const XT* f, XT* x, cudaStream_t
   n /= NV;   // nodes
   const unsigned g = grid_for(n);
   switch (NV) {
-    case 1: k_iso_mapply<1, VT, XT, AT><<<g, 256, 0, s>>>(n, M, f, x); break;
-    case 2: k_iso_mapply<2, VT, XT, AT><<<g, 256, 0, s>>>(n, M, f, x); break;
-    case 3: k_iso_mapply<3, VT, XT, AT><<<g, 256, 0, s>>>(n, M, f, x); break;
-    case 4: k_iso_mapply<4, VT, XT, AT><<<g, 256, 0, s>>>(n, M, f, x); break;
+    case 1: ::gbs::launch_k(k_iso_mapply<1, VT, XT, AT>, g, 256, 0, s, n, M, f, x); break;
+    case 2: ::gbs::launch_k(k_iso_mapply<2, VT, XT, AT>, g, 256, 0, s, n, M, f, x); break;
+    case 3: ::gbs::launch_k(k_iso_mapply<3, VT, XT, AT>, g, 256, 0, s, n, M, f, x); break;
+    case 4: ::gbs::launch_k(k_iso_mapply<4, VT, XT, AT>, g, 256, 0, s, n, M, f, x); break;
   }
   GBS_LAUNCH_CHECK();
 }
@@ -650,10 +650,10 @@ void iso_cast_mapply(int NV, int64_t n, const VT* M, const double* r64, XT* fin,
   n /= NV;   // nodes
   const unsigned g = grid_for(n);
   switch (NV) {
-    case 1: k_iso_cast_mapply<1, VT, XT, AT><<<g, 256, 0, s>>>(n, M, r64, fin, x); break;
-    case 2: k_iso_cast_mapply<2, VT, XT, AT><<<g, 256, 0, s>>>(n, M, r64, fin, x); break;
-    case 3: k_iso_cast_mapply<3, VT, XT, AT><<<g, 256, 0, s>>>(n, M, r64, fin, x); break;
-    case 4: k_iso_cast_mapply<4, VT, XT, AT><<<g, 256, 0, s>>>(n, M, r64, fin, x); break;
+    case 1: ::gbs::launch_k(k_iso_cast_mapply<1, VT, XT, AT>, g, 256, 0, s, n, M, r64, fin, x); break;
+    case 2: ::gbs::launch_k(k_iso_cast_mapply<2, VT, XT, AT>, g, 256, 0, s, n, M, r64, fin, x); break;
+    case 3: ::gbs::launch_k(k_iso_cast_mapply<3, VT, XT, AT>, g, 256, 0, s, n, M, r64, fin, x); break;
+    case 4: ::gbs::launch_k(k_iso_cast_mapply<4, VT, XT, AT>, g, 256, 0, s, n, M, r64, fin, x); break;
   }
   GBS_LAUNCH_CHECK();
 }
@@ -662,7 +662,7 @@ template <class TI, class TO>
 void cast(int64_t n, const TI* in, TO* out, cudaStream_t s) {
   if (n == 0) return;
   unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16);
-  k_cast<TI, TO><<<g, 256, 0, s>>>(n, in, out);
+  ::gbs::launch_k(k_cast<TI, TO>, g, 256, 0, s, n, in, out);
   GBS_LAUNCH_CHECK();
 }
 
@@ -937,7 +937,7 @@ struct DevAmg {
       y = pp[q];
       q ^= 1;
     }
-    k_vscale<VT, ST><<<g, 256, 0, s>>>(L.n, L.dinv, y, L.wc);   // D^-1 y
+    ::gbs::launch_k(k_vscale<VT, ST>, g, 256, 0, s, L.n, L.dinv, y, L.wc);   // D^-1 y
     GBS_LAUNCH_CHECK();
     const ST* z = L.wc;
     for (int k = 0; k < ilu_sweeps; ++k) {   // forward: z = D^-1 y - Us z; transposed: t = t0 - L^T t
@@ -971,7 +971,7 @@ struct DevAmg {
     if (L.ilu) {   // xout = xin + omega S (f - A xin)
       resid<TR>(L, xin, f, L.r, s);
       const ST* z = ilu_apply<TR>(L, L.r, s);
-      k_vaxpy<ST><<<grid_for(L.n), 256, 0, s>>>(L.n, xin, (ST)ilu_omega, z, xout);
+      ::gbs::launch_k(k_vaxpy<ST>, grid_for(L.n), 256, 0, s, L.n, xin, (ST)ilu_omega, z, xout);
       GBS_LAUNCH_CHECK();
     } else if (L.iso) {   // diag(m) (x) I is symmetric: the transposed sweep uses S^T only
       if (TR) iso_relax<VT, ST, AT>(B, L.AcT, L.As, false, L.M, f, xin, xout, s);
@@ -997,18 +997,18 @@ struct DevAmg {
     if (L.fused == 2) {
       const unsigned g = grid_for((int64_t)L.AMb.nslices * 32);
       switch (B) {
-        case 1: k_bsell_presmooth<1, VT, ST, AT><<<g, 256, 0, s>>>(L.AMb, L.M, f, x, r); break;
-        case 2: k_bsell_presmooth<2, VT, ST, AT><<<g, 256, 0, s>>>(L.AMb, L.M, f, x, r); break;
-        case 3: k_bsell_presmooth<3, VT, ST, AT><<<g, 256, 0, s>>>(L.AMb, L.M, f, x, r); break;
-        case 4: k_bsell_presmooth<4, VT, ST, AT><<<g, 256, 0, s>>>(L.AMb, L.M, f, x, r); break;
+        case 1: ::gbs::launch_k(k_bsell_presmooth<1, VT, ST, AT>, g, 256, 0, s, L.AMb, L.M, f, x, r); break;
+        case 2: ::gbs::launch_k(k_bsell_presmooth<2, VT, ST, AT>, g, 256, 0, s, L.AMb, L.M, f, x, r); break;
+        case 3: ::gbs::launch_k(k_bsell_presmooth<3, VT, ST, AT>, g, 256, 0, s, L.AMb, L.M, f, x, r); break;
+        case 4: ::gbs::launch_k(k_bsell_presmooth<4, VT, ST, AT>, g, 256, 0, s, L.AMb, L.M, f, x, r); break;
       }
     } else {
       const unsigned g = grid_for((int64_t)(L.AMs.nslices / B) * 32);
       switch (B) {
-        case 1: k_sell_presmooth_direct<1, VT, ST, AT><<<g, 256, 0, s>>>(L.AMs, L.M, f, x, r); break;
-        case 2: k_sell_presmooth_direct<2, VT, ST, AT><<<g, 256, 0, s>>>(L.AMs, L.M, f, x, r); break;
-        case 3: k_sell_presmooth_direct<3, VT, ST, AT><<<g, 256, 0, s>>>(L.AMs, L.M, f, x, r); break;
-        case 4: k_sell_presmooth_direct<4, VT, ST, AT><<<g, 256, 0, s>>>(L.AMs, L.M, f, x, r); break;
+        case 1: ::gbs::launch_k(k_sell_presmooth_direct<1, VT, ST, AT>, g, 256, 0, s, L.AMs, L.M, f, x, r); break;
+        case 2: ::gbs::launch_k(k_sell_presmooth_direct<2, VT, ST, AT>, g, 256, 0, s, L.AMs, L.M, f, x, r); break;
+        case 3: ::gbs::launch_k(k_sell_presmooth_direct<3, VT, ST, AT>, g, 256, 0, s, L.AMs, L.M, f, x, r); break;
+        case 4: ::gbs::launch_k(k_sell_presmooth_direct<4, VT, ST, AT>, g, 256, 0, s, L.AMs, L.M, f, x, r); break;
       }
     }
     GBS_LAUNCH_CHECK();
@@ -1033,7 +1033,7 @@ struct DevAmg {
     }
     if (l + 1 == lev.size()) {
       const ST* Ai = TR ? AinvT : Ainv;
-      k_gemv<ST, ST, AT><<<grid_for((int64_t)nc * 32), 256, 0, s>>>(nc, Ai, f, out);
+      ::gbs::launch_k(k_gemv<ST, ST, AT>, grid_for((int64_t)nc * 32), 256, 0, s, nc, Ai, f, out);
       GBS_LAUNCH_CHECK();
       if (z64) cast<ST, double>(nc, out, z64, s);
       return;
@@ -1048,7 +1048,7 @@ struct DevAmg {
     if (pre >= 1) {
       if (L.ilu) {
         const ST* z = ilu_apply<TR>(L, f, s);
-        k_vaxpy<ST><<<grid_for(L.n), 256, 0, s>>>(L.n, (const ST*)nullptr, (ST)ilu_omega, z, x);
+        ::gbs::launch_k(k_vaxpy<ST>, grid_for(L.n), 256, 0, s, L.n, (const ST*)nullptr, (ST)ilu_omega, z, x);
         GBS_LAUNCH_CHECK();
       } else if (L.fused && !TR && pre == 1 && !(L.fused == 3 && r64)) {
         presmooth_resid(L, f, x, L.r, s);   // x = M f and r = f - A x in one pass
@@ -1106,10 +1106,10 @@ struct DevAmg {
     }
     const int nb = L.A.nbr;
     switch (B) {
-      case 1: k_cast_mapply<1, TR, VT, ST, AT><<<grid_for(row_threads<1>(nb)), 256, 0, s>>>(nb, L.M, r64, fin, x); break;
-      case 2: k_cast_mapply<2, TR, VT, ST, AT><<<grid_for(row_threads<2>(nb)), 256, 0, s>>>(nb, L.M, r64, fin, x); break;
-      case 3: k_cast_mapply<3, TR, VT, ST, AT><<<grid_for(row_threads<3>(nb)), 256, 0, s>>>(nb, L.M, r64, fin, x); break;
-      case 4: k_cast_mapply<4, TR, VT, ST, AT><<<grid_for(row_threads<4>(nb)), 256, 0, s>>>(nb, L.M, r64, fin, x); break;
+      case 1: ::gbs::launch_k(k_cast_mapply<1, TR, VT, ST, AT>, grid_for(row_threads<1>(nb)), 256, 0, s, nb, L.M, r64, fin, x); break;
+      case 2: ::gbs::launch_k(k_cast_mapply<2, TR, VT, ST, AT>, grid_for(row_threads<2>(nb)), 256, 0, s, nb, L.M, r64, fin, x); break;
+      case 3: ::gbs::launch_k(k_cast_mapply<3, TR, VT, ST, AT>, grid_for(row_threads<3>(nb)), 256, 0, s, nb, L.M, r64, fin, x); break;
+      case 4: ::gbs::launch_k(k_cast_mapply<4, TR, VT, ST, AT>, grid_for(row_threads<4>(nb)), 256, 0, s, nb, L.M, r64, fin, x); break;
     }
     GBS_LAUNCH_CHECK();
   }
@@ -1239,6 +1239,7 @@ struct AmgPrecond final : DevPrecond {
 // One thread a node: its NV + 1 interleaved FP64 entries load as one run.
 template <int NV, class ST>
 __global__ void k_gather_u(int nn, const double* __restrict__ r, ST* __restrict__ fu) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
        i += (int64_t)gridDim.x * blockDim.x) {
     double v[NV + 1];
@@ -1256,6 +1257,7 @@ __global__ void k_gather_u(int nn, const double* __restrict__ r, ST* __restrict_
 template <int NV, class VT, class ST>
 __global__ void k_schur_q_csr(DevCsr<VT> C, const double* __restrict__ r, const ST* __restrict__ u,
                               ST* __restrict__ q) {
+  GBS_GRID_DEP();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C.n; i += gridDim.x * blockDim.x) {
     ST acc = ST(0);
     for (int k = C.rp[i]; k < C.rp[i + 1]; ++k) acc += cvt<ST>(C.val[k]) * u[C.col[k]];
@@ -1266,6 +1268,7 @@ __global__ void k_schur_q_csr(DevCsr<VT> C, const double* __restrict__ r, const 
 template <class VT, class ST>
 __global__ void k_schur_u_csr(DevCsr<VT> C, const ST* __restrict__ fu, const ST* __restrict__ p,
                               ST* __restrict__ fu2) {
+  GBS_GRID_DEP();
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < C.n; t += gridDim.x * blockDim.x) {
     ST acc = fu[t];
     for (int k = C.rp[t]; k < C.rp[t + 1]; ++k) acc -= cvt<ST>(C.val[k]) * p[C.col[k]];
@@ -1275,6 +1278,7 @@ __global__ void k_schur_u_csr(DevCsr<VT> C, const ST* __restrict__ fu, const ST*
 // q_i = r_p,i (pressure part of an interleaved vector)
 template <int NV, class ST>
 __global__ void k_gather_p(int nn, const double* __restrict__ r, ST* __restrict__ q) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
        i += (int64_t)gridDim.x * blockDim.x)
     q[i] = (ST)r[i * (NV + 1) + NV];
@@ -1283,6 +1287,7 @@ __global__ void k_gather_p(int nn, const double* __restrict__ r, ST* __restrict_
 template <class VT, class ST>
 __global__ void k_diag_apply(int nn, const VT* __restrict__ m, const ST* __restrict__ q,
                              ST* __restrict__ p) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = cvt<ST>(m[i]) * q[i];
@@ -1290,6 +1295,7 @@ __global__ void k_diag_apply(int nn, const VT* __restrict__ m, const ST* __restr
 template <int NV, class ST>
 __global__ void k_scatter_z(int nn, const ST* __restrict__ u, const ST* __restrict__ p,
                             double* __restrict__ z) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
        i += (int64_t)gridDim.x * blockDim.x) {
     double v[NV + 1];
@@ -1358,7 +1364,7 @@ struct SchurPrecond final : DevPrecond {
 
   void pressure(const ST* qin, ST* pout, bool tr, cudaStream_t s) {
     if (MS) {
-      k_diag_apply<VT, ST><<<grid_for(nn), 256, 0, s>>>(nn, MS, qin, pout);
+      ::gbs::launch_k(k_diag_apply<VT, ST>, grid_for(nn), 256, 0, s, nn, MS, qin, pout);
       GBS_LAUNCH_CHECK();
     } else {
       S.vcycle(qin, pout, tr, s);
@@ -1373,32 +1379,32 @@ struct SchurPrecond final : DevPrecond {
   void run(const double* r, double* z, bool tr, cudaStream_t s) {
     const unsigned g = grid_for((int64_t)nn * NV);
     const unsigned gn = grid_for(nn);
-    k_gather_u<NV, ST><<<gn, 256, 0, s>>>(nn, r, fu);
+    ::gbs::launch_k(k_gather_u<NV, ST>, gn, 256, 0, s, nn, r, fu);
     GBS_LAUNCH_CHECK();
     const ST* uout = u;
     if (order == 1 && tr) {
-      k_gather_p<NV, ST><<<gn, 256, 0, s>>>(nn, r, q);
+      ::gbs::launch_k(k_gather_p<NV, ST>, gn, 256, 0, s, nn, r, q);
       GBS_LAUNCH_CHECK();
       pressure(q, p, true, s);
-      k_schur_u_csr<VT, ST><<<g, 256, 0, s>>>(DcT, fu, p, fu2);
+      ::gbs::launch_k(k_schur_u_csr<VT, ST>, g, 256, 0, s, DcT, fu, p, fu2);
       GBS_LAUNCH_CHECK();
       A.vcycle(fu2, u, true, s);
     } else {
       A.vcycle(fu, u1, tr, s);
       // forward: q = r_p - D u1; transposed: q = r_p - G^T u1
-      k_schur_q_csr<NV, VT, ST><<<gn, 256, 0, s>>>(tr ? GcT : Dc, r, u1, q);
+      ::gbs::launch_k(k_schur_q_csr<NV, VT, ST>, gn, 256, 0, s, tr ? GcT : Dc, r, u1, q);
       GBS_LAUNCH_CHECK();
       pressure(q, p, tr, s);
       if (order == 1) {
         uout = u1;
       } else {
         // forward: fu2 = fu - G p; transposed: fu2 = fu - D^T p
-        k_schur_u_csr<VT, ST><<<g, 256, 0, s>>>(tr ? DcT : Gc, fu, p, fu2);
+        ::gbs::launch_k(k_schur_u_csr<VT, ST>, g, 256, 0, s, tr ? DcT : Gc, fu, p, fu2);
         GBS_LAUNCH_CHECK();
         A.vcycle(fu2, u, tr, s);
       }
     }
-    k_scatter_z<NV, ST><<<gn, 256, 0, s>>>(nn, uout, p, z);
+    ::gbs::launch_k(k_scatter_z<NV, ST>, gn, 256, 0, s, nn, uout, p, z);
     GBS_LAUNCH_CHECK();
   }
 

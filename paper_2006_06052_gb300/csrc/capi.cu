@@ -66,9 +66,18 @@ struct Handle {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // BiCGStab iteration, fwd / adjoint
   int64_t gnodes[2] = {0, 0};                     // kernels per graph replay
-  ~Handle() {
+  // GMRES: the device part of Arnoldi step j (basis size j + 1), fwd / adjoint
+  std::vector<cudaGraphExec_t> garn[2];
+  std::vector<int64_t> garn_nodes[2];
+  void drop_graphs() {
     for (auto& g : gexec)
-      if (g) cudaGraphExecDestroy(g);
+      if (g) cudaGraphExecDestroy(g), g = nullptr;
+    for (auto& v : garn)
+      for (auto& g : v)
+        if (g) cudaGraphExecDestroy(g), g = nullptr;
+  }
+  ~Handle() {
+    drop_graphs();
     if (cap) cudaStreamDestroy(cap);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -371,11 +380,11 @@ void bicg_iteration(Handle& h, bool tr, cudaStream_t s) {
   NvtxRange range("BiCGStab iteration");
   const int64_t n = h.n;
   const unsigned g = vgrid(n, h.red.cap);
-  k_bicg_p<<<g, 256, 0, s>>>(n, h.r, h.v, h.p, h.sc);
+  ::gbs::launch_k(k_bicg_p, g, 256, 0, s, n, h.r, h.v, h.p, h.sc);
   GBS_LAUNCH_CHECK();
   h.pc->apply(h.p, h.ph, tr, s);
   outer(h, tr, SPMV_SET, h.ph, nullptr, h.v, h.rhat, 0, 0, FIN_ALPHA, true, s);
-  k_bicg_s<<<g, 256, 0, s>>>(n, h.r, h.v, h.s, h.sc);
+  ::gbs::launch_k(k_bicg_s, g, 256, 0, s, n, h.r, h.v, h.s, h.sc);
   GBS_LAUNCH_CHECK();
   h.pc->apply(h.s, h.sh, tr, s);
   outer(h, tr, SPMV_SET, h.sh, nullptr, h.t, h.s, 1, 1, FIN_OMEGA, true, s);
@@ -383,25 +392,23 @@ void bicg_iteration(Handle& h, bool tr, cudaStream_t s) {
   GBS_LAUNCH_CHECK();
 }
 
-void run_iteration(Handle& h, bool tr, cudaStream_t s) {
-  if (!h.prm.use_graph) {
-    bicg_iteration(h, tr, s);
-    return;
-  }
-  cudaGraphExec_t& ge = h.gexec[tr ? 1 : 0];
+// Run body(stream) on s from a CUDA graph, captured on h.cap at the first
+// call and kept in ge (nodes: kernels a replay launches).
+template <class F>
+void replay(Handle& h, cudaGraphExec_t& ge, int64_t& nodes, cudaStream_t s, F&& body) {
   if (!ge) {
     cudaGraph_t g = nullptr;
     GBS_CUDA(cudaStreamBeginCapture(h.cap, cudaStreamCaptureModeThreadLocal));
     const int64_t before = launch_count();
     try {
-      bicg_iteration(h, tr, h.cap);
+      body(h.cap);
     } catch (...) {
       cudaStreamEndCapture(h.cap, &g);
       if (g) cudaGraphDestroy(g);
       throw;
     }
-    h.gnodes[tr ? 1 : 0] = launch_count() - before;
-    count_launch(-(launch_count() - before));  // captured, not executed
+    nodes = launch_count() - before;
+    count_launch(-nodes);  // captured, not executed
     GBS_CUDA(cudaStreamEndCapture(h.cap, &g));
     cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
     cudaGraphDestroy(g);
@@ -411,7 +418,16 @@ void run_iteration(Handle& h, bool tr, cudaStream_t s) {
     }
   }
   GBS_CUDA(cudaGraphLaunch(ge, s));
-  count_launch(h.gnodes[tr ? 1 : 0]);
+  count_launch(nodes);
+}
+
+void run_iteration(Handle& h, bool tr, cudaStream_t s) {
+  if (!h.prm.use_graph) {
+    bicg_iteration(h, tr, s);
+    return;
+  }
+  replay(h, h.gexec[tr ? 1 : 0], h.gnodes[tr ? 1 : 0], s,
+         [&](cudaStream_t cs) { bicg_iteration(h, tr, cs); });
 }
 
 gbs_status finish(Handle& h, gbs_info* info, int iters, int repl, double rel, bool conv,
@@ -493,7 +509,7 @@ gbs_status solve_bicgstab(Handle& h, const double* b, double* x, bool tr, cudaSt
       }
       if (claim) {
         GBS_CUDA(cudaMemcpyAsync(h.rhat, h.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        k_set_restart<<<1, 1, 0, s>>>(h.sc);
+        ::gbs::launch_k(k_set_restart, 1, 1, 0, s, h.sc);
         GBS_LAUNCH_CHECK();
       }
       if (h.sc_host[S_OMEGA] == 0.0 && !claim) {
@@ -561,6 +577,50 @@ void givens(double a, double b, double& c, double& sn) {
   sn = b / r;
 }
 
+// The device part of GMRES Arnoldi step j: w = K M^-1 v_j, its classical
+// Gram-Schmidt coefficients against v_0 .. v_j (h[0..j], and ||w|| for
+// h[j+1]), w -= V h, v_{j+1} = w / ||w||.
+void arnoldi_step(Handle& h, int j, bool tr, cudaStream_t s) {
+  const int64_t n = h.n;
+  const unsigned g = vgrid(n, h.red.cap);
+  double* w = h.V + (size_t)(j + 1) * n;
+  h.pc->apply(h.V + (size_t)j * n, h.z, tr, s);
+  outer(h, tr, SPMV_SET, h.z, nullptr, w, nullptr, 0, 0, FIN_STORE, false, s);
+  const int J = j + 1;
+  NvtxRange orth("GMRES orthogonalisation");
+  launch_resident(k_multidot, h.red.cap, s, n, h.V, J, w, h.hcol, h.red, 5, nullptr);
+  GBS_LAUNCH_CHECK();
+  launch_resident(k_orth, h.red.cap, s, n, h.V, J, w, h.hcol, nullptr, h.red, 6, nullptr);
+  GBS_LAUNCH_CHECK();
+  if (h.prm.gmres_reorth != 0) {
+    // the second pass: always, or when k_orth flagged a drop of ||w||
+    const double* gate = h.prm.gmres_reorth == 2 ? nullptr : h.sc + S_REORTH;
+    launch_resident(k_multidot, h.red.cap, s, n, h.V, J, w, h.hcol2, h.red, 7, gate);
+    GBS_LAUNCH_CHECK();
+    launch_resident(k_orth, h.red.cap, s, n, h.V, J, w, h.hcol2, h.hcol, h.red, 8, gate);
+    GBS_LAUNCH_CHECK();
+  }
+  ::gbs::launch_k(k_normalize, g, 256, 0, s, n, w, h.sc, h.hcol + J);
+  GBS_LAUNCH_CHECK();
+}
+
+// Arnoldi step j replayed from its own CUDA graph (one per basis size,
+// captured the first time a solve reaches it), or launched directly when
+// use_graph is 0.
+void run_arnoldi(Handle& h, int j, bool tr, cudaStream_t s) {
+  if (!h.prm.use_graph) {
+    arnoldi_step(h, j, tr, s);
+    return;
+  }
+  auto& ge = h.garn[tr ? 1 : 0];
+  auto& nodes = h.garn_nodes[tr ? 1 : 0];
+  if ((int)ge.size() < h.m) {
+    ge.resize(h.m, nullptr);
+    nodes.resize(h.m, 0);
+  }
+  replay(h, ge[j], nodes[j], s, [&](cudaStream_t cs) { arnoldi_step(h, j, tr, cs); });
+}
+
 gbs_status solve_gmres(Handle& h, const double* b, double* x, bool tr, cudaStream_t s,
                        gbs_info* info) {
   const int64_t n = h.n;
@@ -599,7 +659,7 @@ gbs_status solve_gmres(Handle& h, const double* b, double* x, bool tr, cudaStrea
       break;
     }
     if (it >= h.prm.maxiter) break;
-    k_scale_rr<<<g, 256, 0, s>>>(n, h.r, h.V, h.sc);
+    ::gbs::launch_k(k_scale_rr, g, 256, 0, s, n, h.r, h.V, h.sc);
     GBS_LAUNCH_CHECK();
     std::fill(H.begin(), H.end(), 0.0);
     std::fill(gv.begin(), gv.end(), 0.0);
@@ -607,25 +667,8 @@ gbs_status solve_gmres(Handle& h, const double* b, double* x, bool tr, cudaStrea
     int j = 0;
     while (j < m && it < h.prm.maxiter) {
       NvtxRange step("GMRES Arnoldi step");
-      double* w = h.V + (size_t)(j + 1) * n;
-      h.pc->apply(h.V + (size_t)j * n, h.z, tr, s);
-      outer(h, tr, SPMV_SET, h.z, nullptr, w, nullptr, 0, 0, FIN_STORE, false, s);
       const int J = j + 1;
-      NvtxRange orth("GMRES orthogonalisation");
-      launch_resident(k_multidot, h.red.cap, s, n, h.V, J, w, h.hcol, h.red, 5, nullptr);
-      GBS_LAUNCH_CHECK();
-      launch_resident(k_orth, h.red.cap, s, n, h.V, J, w, h.hcol, nullptr, h.red, 6, nullptr);
-      GBS_LAUNCH_CHECK();
-      if (h.prm.gmres_reorth != 0) {
-        // the second pass: always, or when k_orth flagged a drop of ||w||
-        const double* gate = h.prm.gmres_reorth == 2 ? nullptr : h.sc + S_REORTH;
-        launch_resident(k_multidot, h.red.cap, s, n, h.V, J, w, h.hcol2, h.red, 7, gate);
-        GBS_LAUNCH_CHECK();
-        launch_resident(k_orth, h.red.cap, s, n, h.V, J, w, h.hcol2, h.hcol, h.red, 8, gate);
-        GBS_LAUNCH_CHECK();
-      }
-      k_normalize<<<g, 256, 0, s>>>(n, w, h.sc, h.hcol + J);
-      GBS_LAUNCH_CHECK();
+      run_arnoldi(h, j, tr, s);
       GBS_CUDA(cudaMemcpyAsync(h.h_host, h.hcol, sizeof(double) * (J + 1), cudaMemcpyDeviceToHost, s));
       GBS_CUDA(cudaStreamSynchronize(s));
       for (int i = 0; i <= J; ++i) H[(size_t)i * m + j] = h.h_host[i];
@@ -651,10 +694,10 @@ gbs_status solve_gmres(Handle& h, const double* b, double* x, bool tr, cudaStrea
       y[i] = acc / H[(size_t)i * m + i];
     }
     GBS_CUDA(cudaMemcpyAsync(h.ydev, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
-    k_combine<<<g, 256, 0, s>>>(n, h.V, j, h.ydev, h.u);
+    ::gbs::launch_k(k_combine, g, 256, 0, s, n, h.V, j, h.ydev, h.u);
     GBS_LAUNCH_CHECK();
     h.pc->apply(h.u, h.z, tr, s);
-    k_axpy<<<g, 256, 0, s>>>(n, 1.0, h.z, h.xi);
+    ::gbs::launch_k(k_axpy, g, 256, 0, s, n, 1.0, h.z, h.xi);
     GBS_LAUNCH_CHECK();
     GBS_CUDA(cudaStreamSynchronize(s));  // y is a pageable host buffer
   }
@@ -682,11 +725,7 @@ void settle_k_format(Handle& h, cudaStream_t s) {
   if (flag) {
     h.k_csr = false;
     // captured iterations launch the CSR kernel: capture again
-    for (int i = 0; i < 2; ++i)
-      if (h.gexec[i]) {
-        cudaGraphExecDestroy(h.gexec[i]);
-        h.gexec[i] = nullptr;
-      }
+    h.drop_graphs();
   }
 }
 
@@ -766,10 +805,10 @@ gbs_status solve_idrs(Handle& h, const double* b, double* x, bool tr, cudaStream
       }
       double* Gk = h.Gidr + (size_t)k * n;
       double* Uk = h.Uidr + (size_t)k * n;
-      k_idr_comb<<<g, 256, 0, s>>>(n, h.v, 1.0, h.r, Gk, sd - k, cn);   // v = r - G[k:] c
+      ::gbs::launch_k(k_idr_comb, g, 256, 0, s, n, h.v, 1.0, h.r, Gk, sd - k, cn);   // v = r - G[k:] c
       GBS_LAUNCH_CHECK();
       h.pc->apply(h.v, h.ph, tr, s);                                   // v = M^-1 v
-      k_idr_comb<<<g, 256, 0, s>>>(n, Uk, om, h.ph, Uk, sd - k, cp);    // U_k = U[k:] c + om v
+      ::gbs::launch_k(k_idr_comb, g, 256, 0, s, n, Uk, om, h.ph, Uk, sd - k, cp);    // U_k = U[k:] c + om v
       GBS_LAUNCH_CHECK();
       outer(h, tr, SPMV_SET, Uk, nullptr, Gk, nullptr, 0, 0, FIN_STORE, false, s);  // G_k = K U_k
       ++it;
@@ -782,9 +821,9 @@ gbs_status solve_idrs(Handle& h, const double* b, double* x, bool tr, cudaStream
       if (k > 0) {
         Coefs ca{};
         for (int i = 0; i < k; ++i) ca.c[i] = -al[i];
-        k_idr_comb<<<g, 256, 0, s>>>(n, Gk, 1.0, Gk, h.Gidr, k, ca);
+        ::gbs::launch_k(k_idr_comb, g, 256, 0, s, n, Gk, 1.0, Gk, h.Gidr, k, ca);
         GBS_LAUNCH_CHECK();
-        k_idr_comb<<<g, 256, 0, s>>>(n, Uk, 1.0, Uk, h.Uidr, k, ca);
+        ::gbs::launch_k(k_idr_comb, g, 256, 0, s, n, Uk, 1.0, Uk, h.Uidr, k, ca);
         GBS_LAUNCH_CHECK();
       }
       for (int i = k; i < sd; ++i) {
@@ -1140,7 +1179,7 @@ gbs_status gbs_sampled_outer(const gbs_hierarchy* hh, const double* lam, const d
     need_aligned(grad, "grad");
     cudaStream_t s = S(stream);
 #define GBS_SO(BB)                                                                    \
-  k_sampled_outer<BB><<<grid_for(row_threads<BB>(h.K.nbr)), 256, 0, s>>>(h.K, lam, x, \
+  ::gbs::launch_k(k_sampled_outer<BB>, grid_for(row_threads<BB>(h.K.nbr)), 256, 0, s, h.K, lam, x, \
                                                                          alpha, grad)
     switch (h.B) {
       case 1: GBS_SO(1); break;
@@ -1165,11 +1204,11 @@ gbs_status gbs_update_values(gbs_hierarchy* hh, const double* vals, void* stream
                              cudaMemcpyDeviceToDevice, s));
     if (h.k_csr) {
       if (h.k_sell)
-        k_gather_sell<<<vgrid(h.kmap_n, h.red.cap), 256, 0, s>>>(h.kmap_n, h.kmap, h.Kval, h.kcval);
+        ::gbs::launch_k(k_gather_sell, vgrid(h.kmap_n, h.red.cap), 256, 0, s, h.kmap_n, h.kmap, h.Kval, h.kcval);
       else
-        k_gather_vals<<<vgrid((int64_t)h.Kh.val.size(), h.red.cap), 256, 0, s>>>(h.kmap_n, h.kmap, h.Kval, h.kcval);
+        ::gbs::launch_k(k_gather_vals, vgrid((int64_t)h.Kh.val.size(), h.red.cap), 256, 0, s, h.kmap_n, h.kmap, h.Kval, h.kcval);
       GBS_LAUNCH_CHECK();
-      k_check_outside<<<vgrid((int64_t)h.Kh.val.size(), h.red.cap), 256, 0, s>>>((int64_t)h.Kh.val.size(), h.kzero,
+      ::gbs::launch_k(k_check_outside, vgrid((int64_t)h.Kh.val.size(), h.red.cap), 256, 0, s, (int64_t)h.Kh.val.size(), h.kzero,
                                                                       h.Kval, h.kflag);
       GBS_LAUNCH_CHECK();
       h.k_check_pending = true;

@@ -64,6 +64,7 @@ template <int NV, int S, int MODE, class VT, class XT, class YT, class AT>
 __global__ void __launch_bounds__(256, 4) k_iso_csr_spmv(DevCsr<VT> A, const XT* __restrict__ x,
                                                       const YT* __restrict__ f,
                                                       YT* __restrict__ y) {
+  GBS_GRID_DEP();
   RowMapS<1, S> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   const bool ok = m.lane_ok && m.brow < A.n;
   AT acc[NV];
@@ -111,6 +112,7 @@ template <int NV, int G, int MODE, class VT, class XT, class YT, class AT>
 __global__ void __launch_bounds__(G) k_iso_csr_spmv_cta(DevCsr<VT> A, const XT* __restrict__ x,
                                                         const YT* __restrict__ f,
                                                         YT* __restrict__ y) {
+  GBS_GRID_DEP();
   const int row = blockIdx.x;   // the grid has one CTA per row
   AT acc[NV];
   iso_cta_row<NV, G, VT, XT, AT>(A, x, row, acc);
@@ -121,6 +123,7 @@ __global__ void __launch_bounds__(G) k_iso_csr_relax_cta(DevCsr<VT> A, const VT*
                                                          const XT* __restrict__ f,
                                                          const XT* __restrict__ x,
                                                          OT* __restrict__ xo) {
+  GBS_GRID_DEP();
   const int row = blockIdx.x;
   AT acc[NV];
   iso_cta_row<NV, G, VT, XT, AT>(A, x, row, acc);
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(256, 4) k_iso_csr_relax(DevCsr<VT> A, const VT
                                                        const XT* __restrict__ f,
                                                        const XT* __restrict__ x,
                                                        OT* __restrict__ xo) {
+  GBS_GRID_DEP();
   RowMapS<1, S> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   const bool ok = m.lane_ok && m.brow < A.n;
   AT acc[NV];
@@ -248,6 +252,7 @@ template <int NV, int MODE, class VT, class XT, class YT, class AT>
 __global__ void __launch_bounds__(256, 4) k_iso_sell_spmv(DevSell<VT> A, const XT* __restrict__ x,
                                                        const YT* __restrict__ f,
                                                        YT* __restrict__ y) {
+  GBS_GRID_DEP();
   const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (q >= A.nslices) return;   // warp-uniform
   const int lane = threadIdx.x & 31;
@@ -265,6 +270,7 @@ __global__ void __launch_bounds__(256, 4) k_iso_sell_relax(DevSell<VT> A, const 
                                                         const XT* __restrict__ f,
                                                         const XT* __restrict__ x,
                                                         OT* __restrict__ xo) {
+  GBS_GRID_DEP();
   const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (q >= A.nslices) return;
   const int lane = threadIdx.x & 31;
@@ -290,6 +296,7 @@ __global__ void __launch_bounds__(256, 4) k_iso_sell_presmooth(DevSell<VT> AM,
                                                             const XT* __restrict__ f,
                                                             XT* __restrict__ x,
                                                             XT* __restrict__ r) {
+  GBS_GRID_DEP();
   const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (q >= AM.nslices) return;
   const int lane = threadIdx.x & 31;
@@ -318,6 +325,7 @@ __global__ void __launch_bounds__(256, 4) k_iso_sell_presmooth_otf(DevSell<VT> A
                                                                 const XT* __restrict__ f,
                                                                 XT* __restrict__ x,
                                                                 XT* __restrict__ r) {
+  GBS_GRID_DEP();
   const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (q >= A.nslices) return;
   const int lane = threadIdx.x & 31;
@@ -342,6 +350,7 @@ __global__ void __launch_bounds__(256, 4) k_iso_sell_presmooth_otf(DevSell<VT> A
 template <int NV, class VT, class XT, class AT>
 __global__ void k_iso_mapply(int64_t nn, const VT* __restrict__ M, const XT* __restrict__ f,
                              XT* __restrict__ x) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
        i += (int64_t)gridDim.x * blockDim.x) {
     const AT mi = cvt<AT>(M[i]);
@@ -357,6 +366,7 @@ __global__ void k_iso_mapply(int64_t nn, const VT* __restrict__ M, const XT* __r
 template <int NV, class VT, class XT, class AT>
 __global__ void k_iso_cast_mapply(int64_t nn, const VT* __restrict__ M, const double* __restrict__ r,
                                   XT* __restrict__ fin, XT* __restrict__ x) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
        i += (int64_t)gridDim.x * blockDim.x) {
     const AT mi = cvt<AT>(M[i]);

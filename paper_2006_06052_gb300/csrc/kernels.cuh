@@ -21,9 +21,65 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdlib>
 #include <type_traits>
+#include <utility>
 
 namespace gbs {
+
+// ------------------------------------------- programmatic dependent launch
+// The solve phase is a chain of short dependent kernels (about 40 a
+// BiCGStab iteration, 80 a Schur application), and on the small and
+// mixed-precision levels the gap between one kernel's last CTAs and the
+// next one's first is a large part of each kernel's time.  Every kernel is
+// launched with programmatic stream serialization (launch_k), so the next
+// kernel in the stream may be scheduled while this one finishes; every
+// kernel begins with GBS_GRID_DEP: griddepcontrol.wait, which returns once
+// the preceding grid has completed and its writes are visible (at once when
+// there is none), so no read or write moves ahead of its predecessor; then
+// griddepcontrol.launch_dependents, which lets the following grid launch
+// once every CTA of this one has started.  GBS_PDL=0 launches without the
+// attribute (measurement).
+#define GBS_GRID_DEP()                                           \
+  do {                                                           \
+    asm volatile("griddepcontrol.wait;" ::: "memory");           \
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); \
+  } while (0)
+
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("GBS_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+// fn<<<grid, block, smem, s>>>(a...) with programmatic stream
+// serialization, except while s is being captured into a CUDA graph: in a
+// replayed graph the attribute measured slower (C2 BiCGStab iteration, FP64
+// 23.5 -> 24.3 ms a solve, BF16 12.5 -> 14.0 ms), while stream launches gain
+// (C3 GMRES, FP64 103 -> 98.5 ms, BF16 68.4 -> 63.7 ms).  Errors surface
+// through cudaPeekAtLastError at the caller.
+template <class... KA, class... A>
+inline void launch_k(void (*fn)(KA...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     A&&... a) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (pdl_enabled() && cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    (void)cudaGetLastError();
+    cs = cudaStreamCaptureStatusActive;   // unknown: launch without the attribute
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() && cs == cudaStreamCaptureStatusNone ? 1 : 0;
+  (void)cudaLaunchKernelEx(&cfg, fn, std::forward<A>(a)...);
+}
 
 template <class VT>
 struct DevBsr {
@@ -534,6 +590,7 @@ enum { SPMV_SET = 0, SPMV_RESID = 1, SPMV_ADD = 2 };
 template <int B, int S, bool TR, int MODE, class VT, class XT, class YT, class AT>
 __global__ void __launch_bounds__(256, 4) k_spmv(DevBsr<VT> A, const XT* __restrict__ x,
                                               const YT* __restrict__ f, YT* __restrict__ y) {
+  GBS_GRID_DEP();
   RowMapS<B, S> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   const bool ok = m.lane_ok && m.brow < A.nbr;
   AT acc = ok ? row_dot<B, TR, VT, XT, AT, S>(A, x, m.brow, m.r, m.s) : AT(0);
@@ -549,6 +606,7 @@ __global__ void __launch_bounds__(256, 4) k_spmv(DevBsr<VT> A, const XT* __restr
 template <int B, int G, bool TR, int MODE, class VT, class XT, class YT, class AT>
 __global__ void __launch_bounds__(256, 4) k_spmv_w(DevBsr<VT> A, const XT* __restrict__ x,
                                                 const YT* __restrict__ f, YT* __restrict__ y) {
+  GBS_GRID_DEP();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int brow = (int)(t / G);
   const int g = (int)(t % G);
@@ -568,6 +626,7 @@ template <int B, int G, bool TR, class VT, class XT, class AT>
 __global__ void __launch_bounds__(256, 4) k_relax_w(DevBsr<VT> A, const VT* __restrict__ M,
                                                  const XT* __restrict__ f,
                                                  const XT* __restrict__ x, XT* __restrict__ xo) {
+  GBS_GRID_DEP();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int brow = (int)(t / G);
   const int g = (int)(t % G);
@@ -593,6 +652,7 @@ template <int B, int S, bool TR, class VT, class XT, class AT>
 __global__ void __launch_bounds__(256, 4) k_relax(DevBsr<VT> A, const VT* __restrict__ M,
                                                const XT* __restrict__ f,
                                                const XT* __restrict__ x, XT* __restrict__ xo) {
+  GBS_GRID_DEP();
   RowMapS<B, S> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   const bool ok = m.lane_ok && m.brow < A.nbr;
   const size_t o = (size_t)m.brow * B + m.r;
@@ -736,6 +796,7 @@ __device__ __forceinline__ AT bsell_row_dot(const DevBSell<VT>& A, const XT* __r
 template <int B, int MODE, class VT, class XT, class YT, class AT>
 __global__ void __launch_bounds__(256, 4) k_bsell_spmv(DevBSell<VT> A, const XT* __restrict__ x,
                                                      const YT* __restrict__ f, YT* __restrict__ y) {
+  GBS_GRID_DEP();
   constexpr int R = 32 / B;
   const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (q >= A.nslices) return;
@@ -758,6 +819,7 @@ __global__ void __launch_bounds__(256, 4) k_bsell_relax(DevBSell<VT> A, const VT
                                                       const XT* __restrict__ f,
                                                       const XT* __restrict__ x,
                                                       XT* __restrict__ xo) {
+  GBS_GRID_DEP();
   constexpr int R = 32 / B;
   const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (q >= A.nslices) return;   // warp-uniform
@@ -789,6 +851,7 @@ template <int B, class VT, class XT, class AT>
 __global__ void __launch_bounds__(256, 4) k_bsell_presmooth(DevBSell<VT> AM, const VT* __restrict__ M,
                                                           const XT* __restrict__ f,
                                                           XT* __restrict__ x, XT* __restrict__ r) {
+  GBS_GRID_DEP();
   constexpr int R = 32 / B;
   const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (q >= AM.nslices) return;
@@ -825,6 +888,7 @@ __device__ __forceinline__ AT csr_row_dot(const DevCsr<VT>& A, const XT* __restr
 template <int S, int MODE, class VT, class XT, class YT, class AT>
 __global__ void __launch_bounds__(256, 4) k_csr_spmv(DevCsr<VT> A, const XT* __restrict__ x,
                                                   const YT* __restrict__ f, YT* __restrict__ y) {
+  GBS_GRID_DEP();
   RowMapS<1, S> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   const bool ok = m.lane_ok && m.brow < A.n;
   AT acc = ok ? csr_row_dot<S, VT, XT, AT>(A, x, m.brow, m.s) : AT(0);
@@ -843,6 +907,7 @@ __global__ void __launch_bounds__(256, 4) k_csr_relax(DevCsr<VT> A, const VT* __
                                                    const XT* __restrict__ f,
                                                    const XT* __restrict__ x,
                                                    XT* __restrict__ xo) {
+  GBS_GRID_DEP();
   RowMapS<B, S> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   const int nnodes = A.n / B;
   const bool ok = m.lane_ok && m.brow < nnodes;
@@ -866,6 +931,7 @@ __global__ void __launch_bounds__(256, 4) k_csr_relax(DevCsr<VT> A, const VT* __
 template <int B, bool TR, class VT, class XT, class AT>
 __global__ void __launch_bounds__(256, 4) k_mapply(int nbr, const VT* __restrict__ M,
                                                 const XT* __restrict__ f, XT* __restrict__ x) {
+  GBS_GRID_DEP();
   RowMap<B> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   if (!m.lane_ok || m.brow >= nbr) return;
   AT mr[B], fv[B];
@@ -886,6 +952,7 @@ template <int B, bool TR, class VT, class XT, class AT>
 __global__ void __launch_bounds__(256, 4) k_cast_mapply(int nbr, const VT* __restrict__ M,
                                                      const double* __restrict__ r,
                                                      XT* __restrict__ fin, XT* __restrict__ x) {
+  GBS_GRID_DEP();
   RowMap<B> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   if ((int64_t)(blockIdx.x * (int64_t)blockDim.x + threadIdx.x - (threadIdx.x & 31)) / 32 *
           RowMap<B>::RPW >= nbr)
@@ -911,6 +978,7 @@ __global__ void __launch_bounds__(256, 4) k_cast_mapply(int nbr, const VT* __res
 template <class VT, class XT, class AT>
 __global__ void __launch_bounds__(256, 4) k_gemv(int n, const VT* __restrict__ Ainv,
                                               const XT* __restrict__ f, XT* __restrict__ x) {
+  GBS_GRID_DEP();
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
@@ -924,6 +992,7 @@ __global__ void __launch_bounds__(256, 4) k_gemv(int n, const VT* __restrict__ A
 
 template <class TI, class TO>
 __global__ void k_cast(int64_t n, const TI* __restrict__ in, TO* __restrict__ out) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (TO)cvt<float>(in[i]);
@@ -931,6 +1000,7 @@ __global__ void k_cast(int64_t n, const TI* __restrict__ in, TO* __restrict__ ou
 template <>
 __global__ void k_cast<double, double>(int64_t n, const double* __restrict__ in,
                                        double* __restrict__ out) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = in[i];
@@ -938,6 +1008,7 @@ __global__ void k_cast<double, double>(int64_t n, const double* __restrict__ in,
 template <>
 __global__ void k_cast<float, double>(int64_t n, const float* __restrict__ in,
                                       double* __restrict__ out) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (double)in[i];
@@ -947,6 +1018,7 @@ __global__ void k_cast<float, double>(int64_t n, const float* __restrict__ in,
 template <class VT, class ST>
 __global__ void k_vscale(int64_t n, const VT* __restrict__ sc, const ST* __restrict__ in,
                          ST* __restrict__ out) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = cvt<ST>(sc[i]) * in[i];
@@ -956,6 +1028,7 @@ __global__ void k_vscale(int64_t n, const VT* __restrict__ sc, const ST* __restr
 template <class ST>
 __global__ void k_vaxpy(int64_t n, const ST* __restrict__ x, ST w, const ST* __restrict__ z,
                         ST* __restrict__ out) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = x ? x[i] + w * z[i] : w * z[i];

@@ -47,7 +47,7 @@ enum FinOp {
 // Launch a grid-stride kernel of RED_THREADS threads with resident_grid blocks.
 template <class... KA, class... A>
 inline void launch_resident(void (*fn)(KA...), int cap, cudaStream_t s, A&&... a) {
-  fn<<<resident_grid((const void*)fn, cap, RED_THREADS, 0), RED_THREADS, 0, s>>>(
+  ::gbs::launch_k(fn, resident_grid((const void*)fn, cap, RED_THREADS, 0), RED_THREADS, 0, s, 
       std::forward<A>(a)...);
 }
 
@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(RED_THREADS, 4)
     k_outer(DevBsr<double> K, const double* __restrict__ x, const double* __restrict__ f,
             double* __restrict__ y, const double* __restrict__ w0, int self_dot, Red R, int slot,
             int op, int reduce) {
+  GBS_GRID_DEP();
   static_assert(G <= 32, "outer SpMV groups stay inside a warp");
   double d[2] = {0.0, 0.0};
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -192,6 +193,7 @@ __global__ void __launch_bounds__(RED_THREADS, 4)
     k_outer_n(DevBsr<double> K, const double* __restrict__ x, const double* __restrict__ f,
               double* __restrict__ y, const double* __restrict__ w0, int self_dot, Red R,
               int slot, int op, int reduce) {
+  GBS_GRID_DEP();
   constexpr int RPW = 32 / B;
   double d[2] = {0.0, 0.0};
   const int64_t nwarps = ((int64_t)K.nbr + RPW - 1) / RPW;
@@ -219,6 +221,7 @@ __global__ void __launch_bounds__(RED_THREADS, 4)
     k_outer_csr(DevCsr<double> K, const double* __restrict__ x, const double* __restrict__ f,
                 double* __restrict__ y, const double* __restrict__ w0, int self_dot, Red R,
                 int slot, int op, int reduce) {
+  GBS_GRID_DEP();
   constexpr int RPW = 32 / S;
   double d[2] = {0.0, 0.0};
   const int64_t nwarps = ((int64_t)K.n + RPW - 1) / RPW;
@@ -251,6 +254,7 @@ __global__ void __launch_bounds__(RED_THREADS, 4)
     k_outer_sell(DevSell<double> K, const double* __restrict__ x, const double* __restrict__ f,
                  double* __restrict__ y, const double* __restrict__ w0, int self_dot, Red R,
                  int slot, int op, int reduce) {
+  GBS_GRID_DEP();
   double d[2] = {0.0, 0.0};
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -280,6 +284,7 @@ __global__ void __launch_bounds__(RED_THREADS, 4)
 // Sliced values of K from its block values (map -1: padding).
 static __global__ void k_gather_sell(int64_t n, const int* __restrict__ map,
                                      const double* __restrict__ bval, double* __restrict__ sval) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int m = map[i];
@@ -290,6 +295,7 @@ static __global__ void k_gather_sell(int64_t n, const int* __restrict__ map,
 // CSR values of K from its block values (after gbs_update_values).
 static __global__ void k_gather_vals(int64_t nnz, const int* __restrict__ map,
                                      const double* __restrict__ bval, double* __restrict__ cval) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
        i += (int64_t)gridDim.x * blockDim.x)
     cval[i] = bval[map[i]];
@@ -298,6 +304,7 @@ static __global__ void k_gather_vals(int64_t nnz, const int* __restrict__ map,
 // flag = 1 if any block value outside the CSR pattern (mask bit set) is nonzero.
 static __global__ void k_check_outside(int64_t nvals, const unsigned* __restrict__ zero_mask,
                                        const double* __restrict__ bval, int* __restrict__ flag) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvals;
        i += (int64_t)gridDim.x * blockDim.x)
     if (((zero_mask[i >> 5] >> (i & 31)) & 1u) && bval[i] != 0.0) *flag = 1;
@@ -306,6 +313,7 @@ static __global__ void k_check_outside(int64_t nvals, const unsigned* __restrict
 // p = r + beta (p - omega v), beta = (rho / rho_old) (alpha / omega); p = r on the first step.
 static __global__ void k_bicg_p(int64_t n, const double* __restrict__ r, const double* __restrict__ v,
                          double* __restrict__ p, const double* __restrict__ sc) {
+  GBS_GRID_DEP();
   // the two FP64 divisions once per CTA, not once per thread
   __shared__ double sbeta;
   const bool first = sc[S_FIRST] != 0.0;
@@ -321,6 +329,7 @@ static __global__ void k_bicg_p(int64_t n, const double* __restrict__ r, const d
 // s = r - alpha v
 static __global__ void k_bicg_s(int64_t n, const double* __restrict__ r, const double* __restrict__ v,
                          double* __restrict__ s, const double* __restrict__ sc) {
+  GBS_GRID_DEP();
   const double alpha = sc[S_ALPHA];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -333,6 +342,7 @@ static __global__ void __launch_bounds__(RED_THREADS, 4)
               const double* __restrict__ sh, const double* __restrict__ s,
               const double* __restrict__ t, double* __restrict__ r,
               const double* __restrict__ rhat, Red R, int slot) {
+  GBS_GRID_DEP();
   const double alpha = R.sc[S_ALPHA], omega = R.sc[S_OMEGA];
   double d[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -350,6 +360,7 @@ static __global__ void __launch_bounds__(RED_THREADS, 4)
 static __global__ void __launch_bounds__(RED_THREADS, 4)
     k_dot2(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
            const double* __restrict__ c, Red R, int slot, int op) {
+  GBS_GRID_DEP();
   double d[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -360,6 +371,7 @@ static __global__ void __launch_bounds__(RED_THREADS, 4)
 }
 
 static __global__ void k_set_restart(double* sc) {
+  GBS_GRID_DEP();
   sc[S_RHO] = sc[S_RR];
   sc[S_RHO_OLD] = 1.0;
   sc[S_ALPHA] = 1.0;
@@ -376,6 +388,7 @@ struct Coefs {
 // or V_0: every element reads its inputs before writing.
 static __global__ void k_idr_comb(int64_t n, double* out, double alpha, const double* a,
                                   const double* V, int m, Coefs c) {
+  GBS_GRID_DEP();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
     double acc = a ? alpha * a[e] : 0.0;
@@ -391,6 +404,7 @@ static __global__ void __launch_bounds__(RED_THREADS, 4)
     k_idr_update(int64_t n, double* __restrict__ r, double* __restrict__ x,
                  const double* __restrict__ g, const double* __restrict__ u, double beta, Red R,
                  int slot) {
+  GBS_GRID_DEP();
   double d[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -442,6 +456,7 @@ __device__ __forceinline__ void multidot_pass(int64_t n, const double* __restric
 static __global__ void __launch_bounds__(RED_THREADS, 4)
     k_multidot(int64_t n, const double* __restrict__ V, int J, const double* __restrict__ w,
                double* __restrict__ h, Red R, int slot, const double* __restrict__ gate) {
+  GBS_GRID_DEP();
   if (gate && *gate == 0.0) return;
   __shared__ double sh[RED_THREADS / 32][8];
   __shared__ bool last;
@@ -513,6 +528,7 @@ static __global__ void __launch_bounds__(RED_THREADS, 4)
     k_orth(int64_t n, const double* __restrict__ V, int J, double* __restrict__ w,
            const double* __restrict__ h, double* __restrict__ hacc, Red R, int slot,
            const double* __restrict__ gate) {
+  GBS_GRID_DEP();
   if (gate && *gate == 0.0) return;
   __shared__ double hs[MAX_DOTS];
   for (int i = threadIdx.x; i < J; i += blockDim.x) hs[i] = h[i];
@@ -555,6 +571,7 @@ static __global__ void __launch_bounds__(RED_THREADS, 4)
 // w /= sqrt(sc[S_WW]) (if nonzero); hnext = sqrt(sc[S_WW])
 static __global__ void k_normalize(int64_t n, double* __restrict__ w, const double* __restrict__ sc,
                             double* __restrict__ hnext) {
+  GBS_GRID_DEP();
   const double nrm = sqrt(sc[S_WW]);
   if (blockIdx.x == 0 && threadIdx.x == 0) *hnext = nrm;
   if (nrm == 0.0) return;
@@ -567,6 +584,7 @@ static __global__ void k_normalize(int64_t n, double* __restrict__ w, const doub
 // v = r / sqrt(sc[S_RR])
 static __global__ void k_scale_rr(int64_t n, const double* __restrict__ r, double* __restrict__ v,
                            const double* __restrict__ sc) {
+  GBS_GRID_DEP();
   const double inv = 1.0 / sqrt(sc[S_RR]);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -576,6 +594,7 @@ static __global__ void k_scale_rr(int64_t n, const double* __restrict__ r, doubl
 // u = sum_{i<J} y[i] V_i
 static __global__ void k_combine(int64_t n, const double* __restrict__ V, int J,
                           const double* __restrict__ y, double* __restrict__ u) {
+  GBS_GRID_DEP();
   __shared__ double ys[MAX_DOTS];
   for (int i = threadIdx.x; i < J; i += blockDim.x) ys[i] = y[i];
   __syncthreads();
@@ -588,6 +607,7 @@ static __global__ void k_combine(int64_t n, const double* __restrict__ V, int J,
 }
 
 static __global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  GBS_GRID_DEP();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     y[i] += a * x[i];
@@ -598,6 +618,7 @@ template <int B>
 __global__ void __launch_bounds__(256)
     k_sampled_outer(DevBsr<double> K, const double* __restrict__ lam,
                     const double* __restrict__ x, double alpha, double* __restrict__ grad) {
+  GBS_GRID_DEP();
   RowMap<B> m(blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   if (!m.lane_ok || m.brow >= K.nbr) return;
   const double la = alpha * lam[(size_t)m.brow * B + m.r];

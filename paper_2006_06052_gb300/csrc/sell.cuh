@@ -269,6 +269,7 @@ template <int MODE, class VT, class XT, class YT, class AT>
 __global__ void __launch_bounds__(SELL_WARPS * 32, 2)
     k_sell_spmv(DevSell<VT> A, const XT* __restrict__ x, const YT* __restrict__ f,
                 YT* __restrict__ y) {
+  GBS_GRID_DEP();
   extern __shared__ __align__(128) unsigned char sell_smem[];
   SellStages<VT>& sm = reinterpret_cast<SellStages<VT>*>(sell_smem)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
@@ -292,6 +293,7 @@ template <int B, int MODE, class VT, class XT, class YT, class AT>
 __global__ void __launch_bounds__(SELL_WARPS * 32, 2)
     k_sell_spmv_g(DevSell<VT> A, const XT* __restrict__ x, const YT* __restrict__ f,
                   YT* __restrict__ y) {
+  GBS_GRID_DEP();
   extern __shared__ __align__(128) unsigned char sell_smem[];
   SellStages<VT>& sm = reinterpret_cast<SellStages<VT>*>(sell_smem)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
@@ -323,6 +325,7 @@ template <int B, class VT, class XT, class AT, class OT = XT>
 __global__ void __launch_bounds__(SELL_WARPS * 32, 2)
     k_sell_relax(DevSell<VT> A, const VT* __restrict__ M, const XT* __restrict__ f,
                  const XT* __restrict__ x, OT* __restrict__ xo) {
+  GBS_GRID_DEP();
   extern __shared__ __align__(128) unsigned char sell_smem[];
   SellStages<VT>& sm = reinterpret_cast<SellStages<VT>*>(sell_smem)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
@@ -395,6 +398,7 @@ template <int MODE, class VT, class XT, class YT, class AT>
 __global__ void __launch_bounds__(256, 4) k_sell_spmv_direct(DevSell<VT> A, const XT* __restrict__ x,
                                                         const YT* __restrict__ f,
                                                         YT* __restrict__ y) {
+  GBS_GRID_DEP();
   const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (q >= A.nslices) return;
   const int lane = threadIdx.x & 31;
@@ -414,6 +418,7 @@ __global__ void __launch_bounds__(256, 4) k_sell_spmv_direct_g(DevSell<VT> A,
                                                           const XT* __restrict__ x,
                                                           const YT* __restrict__ f,
                                                           YT* __restrict__ y) {
+  GBS_GRID_DEP();
   const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int nn = A.n / B;
   if (g * 32 >= nn) return;
@@ -442,6 +447,7 @@ __global__ void __launch_bounds__(256, 4) k_sell_relax_direct(DevSell<VT> A, con
                                                          const XT* __restrict__ f,
                                                          const XT* __restrict__ x,
                                                          OT* __restrict__ xo) {
+  GBS_GRID_DEP();
   const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int nn = A.n / B;
   if (g * 32 >= nn) return;
@@ -479,6 +485,7 @@ __global__ void __launch_bounds__(256, 4) k_sell_presmooth_direct(DevSell<VT> AM
                                                              const XT* __restrict__ f,
                                                              XT* __restrict__ x,
                                                              XT* __restrict__ r) {
+  GBS_GRID_DEP();
   const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int nn = AM.n / B;
   if (g * 32 >= nn) return;
@@ -521,7 +528,7 @@ inline void launch_sell(void (*fn)(KA...), size_t smem, int64_t cap, cudaStream_
   }
   const unsigned g = resident_grid((const void*)fn, (int)std::min<int64_t>(cap, 1 << 30),
                                    SELL_WARPS * 32, smem);
-  fn<<<g, SELL_WARPS * 32, smem, s>>>(std::forward<A>(a)...);
+  ::gbs::launch_k(fn, g, SELL_WARPS * 32, smem, s, std::forward<A>(a)...);
 }
 
 }  // namespace gbs
