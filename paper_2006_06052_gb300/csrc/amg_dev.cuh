@@ -278,8 +278,11 @@ DevSell<VT> upload_sell(Arena& ar, const HSell& S, double* err, long long wait, 
 // FP64 (sell.cuh).  The direct kernels would stream only the values of a
 // uniform (stencil) operator in the mixed forms, 2 or 4 bytes an entry
 // against 6 or 8 with staged column indices, but measured slower there
-// (C2 BF16 solve 13.5 ms direct, 13.1 staged): GBS_SELL_DIRECT=1 sends the
-// mixed forms' uniform operators to them, =0 keeps every one staged.
+// (C2 BF16 solve 13.5 ms direct, 13.1 staged; with the value loads and
+// gathers batched four entries deep as in the identity-block kernels,
+// 13.5 ms against 12.4 staged, and FP32 15.9 against 14.7):
+// GBS_SELL_DIRECT=1 sends the mixed forms' uniform operators to them, =0
+// keeps every one staged.
 template <class VT, class AT>
 inline bool sell_direct(const DevSell<VT>& A) {
   if (sizeof(AT) == 8) return true;
