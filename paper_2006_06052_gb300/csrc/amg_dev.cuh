@@ -526,14 +526,23 @@ void set_iso_lanes(DevCsr<VT>& d, int64_t rows, int64_t nnz) {
     else if (v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32) { d.S = v; d.G = 0; }
   }
 }
+// Batched loads in the iso CSR rows (iso_csr_row): FP32 accumulation, or a
+// level small enough to be latency-bound (fewer lanes than LANES_TARGET).
+template <class AT, class VT>
+inline bool iso_batched(const DevCsr<VT>& A) {
+  return sizeof(AT) == 4 || (int64_t)A.n * A.S < LANES_TARGET;
+}
 template <int NV, int MODE, class VT, class XT, class YT, class AT>
 void iso_csr_spmv_nv(const DevCsr<VT>& A, const XT* x, const YT* f, YT* y, cudaStream_t s) {
   if (A.G == 256) {
     ::gbs::launch_k(k_iso_csr_spmv_cta<NV, 256, MODE, VT, XT, YT, AT>, A.n, 256, 0, s, A, x, f, y);
     return;
   }
-#define GBS_ISO(SS) \
-  ::gbs::launch_k(k_iso_csr_spmv<NV, SS, MODE, VT, XT, YT, AT>, grid_for(row_threads_s<1, SS>(A.n)), 256, 0, s, A, x, f, y)
+#define GBS_ISO(SS)                                                                              \
+  if (iso_batched<AT>(A)) ::gbs::launch_k(k_iso_csr_spmv<NV, SS, MODE, VT, XT, YT, AT, true>,    \
+                                          grid_for(row_threads_s<1, SS>(A.n)), 256, 0, s, A, x, f, y); \
+  else ::gbs::launch_k(k_iso_csr_spmv<NV, SS, MODE, VT, XT, YT, AT, false>,                    \
+                       grid_for(row_threads_s<1, SS>(A.n)), 256, 0, s, A, x, f, y)
   switch (A.S) {
     case 2: GBS_ISO(2); break;
     case 4: GBS_ISO(4); break;
@@ -580,8 +589,11 @@ void iso_relax_nv(const DevCsr<VT>& Ac, const DevSell<VT>& As, bool sl, const VT
     ::gbs::launch_k(k_iso_csr_relax_cta<NV, 256, VT, XT, AT, OT>, Ac.n, 256, 0, s, Ac, M, f, x, xo);
     return;
   }
-#define GBS_ISO(SS) \
-  ::gbs::launch_k(k_iso_csr_relax<NV, SS, VT, XT, AT, OT>, grid_for(row_threads_s<1, SS>(Ac.n)), 256, 0, s, Ac, M, f, x, xo)
+#define GBS_ISO(SS)                                                                          \
+  if (iso_batched<AT>(Ac)) ::gbs::launch_k(k_iso_csr_relax<NV, SS, VT, XT, AT, OT, true>,    \
+                                           grid_for(row_threads_s<1, SS>(Ac.n)), 256, 0, s, Ac, M, f, x, xo); \
+  else ::gbs::launch_k(k_iso_csr_relax<NV, SS, VT, XT, AT, OT, false>,                     \
+                       grid_for(row_threads_s<1, SS>(Ac.n)), 256, 0, s, Ac, M, f, x, xo)
   switch (Ac.S) {
     case 2: GBS_ISO(2); break;
     case 4: GBS_ISO(4); break;
