@@ -227,3 +227,25 @@ def test_params_layout_matches_the_header():
     assert (p.ilut_p, p.ilut_tau, p.ilut_sweeps, p.ilut_omega) == (2.0, 1e-2, 2, 1.0)
     assert (p.gmres_reorth, p.wait_log2, p.iso_blocks) == (0, 31, 1)
     assert (p.relax, p.relax_p, p.level_format, p.schur_p, p.schur_order) == (0, 0, 0, 0, 0)
+
+
+@pytest.mark.parametrize("smooth_P", [1, 0])
+def test_velocity_hierarchy_is_identity_blocks(smooth_P):
+    """The library's own setup of the Schur velocity hierarchy (C3 recipe)
+    keeps every stored block of A_l, P_l, R_l and the SPAI0 blocks an exact
+    multiple of I_3 at every level -- the condition under which the device
+    stores those levels as S (x) I_3 (iso_blocks)."""
+    s = si.make_system("c3", N=8)
+    H = _host(s, precond=gb.GBS_PC_SCHUR, krylov=gb.GBS_GMRES, coarse_enough=60,
+              smooth_P=smooth_P)
+    nl = gb.hierarchy_info(H, 0)["nlevels"]
+    assert nl >= 2
+    for l in range(nl - 1):
+        blocks = [gb.export_level(H, 0, l, part)[2] for part in (0, 1, 2)]
+        blocks.append(gb.export_level(H, 0, l, 3).reshape(-1, 3, 3))
+        for v in blocks:
+            off = v.copy()
+            for a in range(3):
+                off[:, a, a] = 0.0
+            assert not off.any(), l
+            assert np.array_equal(v[:, 1, 1], v[:, 0, 0]) and np.array_equal(v[:, 2, 2], v[:, 0, 0]), l

@@ -306,3 +306,64 @@ def test_level_schedule_stop_rules():
                                            relax="jacobi"))
     assert H2.nlevels == 2 and H2.A_coarse.n_brows == 4
     assert H2.levels[0].agg.tolist() == [0, 0, 1, 1, 2, 2, 3, 3]
+
+
+def _velocity_block(N):
+    """The velocity block A_uu of the C3 recipe (3 x 3 blocks) and the
+    scalar S with A_uu = S (x) I_3 (u, v, w share every coefficient)."""
+    from oracle import schur
+    s = si.make_system("c3", N=N)
+    A = schur.split(bsr.from_arrays(s.indptr, s.indices, s.data, 4), 3).A
+    S = bsr.Bsr(A.indptr.copy(), A.indices.copy(), A.data[:, :1, :1].copy(), A.n_bcols)
+    return A, S
+
+
+def _is_identity_multiple(data):
+    B = data.shape[1]
+    off = data.copy()
+    for a in range(B):
+        off[:, a, a] = 0.0
+    diag = np.stack([data[:, a, a] for a in range(B)], 1)
+    return not off.any() and np.array_equal(diag, np.repeat(diag[:, :1], B, 1))
+
+
+@pytest.mark.parametrize("relax", ["spai0", "jacobi"])
+def test_plain_aggregation_of_identity_blocks_is_kron_of_scalar(relax):
+    """Block SA on A = S (x) I_3 with plain aggregation equals the scalar
+    setup on S, Kronecker I_3, at every level: the same aggregates, A_l, P_l,
+    R_l and smoother blocks, and the coarse inverse.  This ties the block
+    code paths (block strength, block SPAI0 / Jacobi inverses, block
+    Galerkin products) to the scalar ones, and it is the structure the
+    library's S (x) I_B layout stores."""
+    A, S = _velocity_block(6)
+    assert np.abs(A.dense() - np.kron(S.dense(), np.eye(3))).max() == 0.0
+    prm = amg.AmgParams(coarse_enough=30, relax=relax, smooth_P=False)
+    Hb, Hs = amg.build_hierarchy(A, prm), amg.build_hierarchy(S, prm)
+    assert len(Hb.levels) == len(Hs.levels) >= 2
+    I3 = np.eye(3)
+    for Lb, Ls in zip(Hb.levels, Hs.levels):
+        np.testing.assert_array_equal(Lb.agg, Ls.agg)
+        for Xb, Xs in ((Lb.A, Ls.A), (Lb.P, Ls.P), (Lb.R, Ls.R)):
+            ref = np.kron(Xs.dense(), I3)
+            assert np.abs(Xb.dense() - ref).max() <= 1e-14 * np.abs(ref).max()
+        mref = np.einsum("i,ab->iab", Ls.M[:, 0, 0], I3)
+        assert np.abs(Lb.M - mref).max() <= 1e-14 * np.abs(mref).max()
+    ref = np.kron(Hs.Ainv_coarse, I3)
+    assert np.abs(Hb.Ainv_coarse - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_smoothed_aggregation_keeps_identity_blocks():
+    """With prolongator smoothing (its damping comes from a power iteration,
+    so the scalar and block setups differ in omega), every stored block of
+    every level -- A_l, P_l, R_l, the SPAI0 blocks -- is still exactly a
+    multiple of I_3, bit for bit, and level 0 aggregates as the scalar S."""
+    A, S = _velocity_block(7)
+    prm = amg.AmgParams(coarse_enough=40)
+    Hb = amg.build_hierarchy(A, prm)
+    assert len(Hb.levels) >= 2
+    for L in Hb.levels:
+        for X in (L.A, L.P, L.R):
+            assert _is_identity_multiple(X.data)
+        assert _is_identity_multiple(L.M)
+    agg_s, _ = amg.aggregate(S, prm.eps_strong)
+    np.testing.assert_array_equal(Hb.levels[0].agg, agg_s)
