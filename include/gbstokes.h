@@ -362,8 +362,10 @@ gbs_status gbs_spmv_dots_noalloc(int32_t n_brows, int32_t n_bcols, int32_t bdim,
 
 /* FP64 FMA throughput of the current device, measured: the best of four
  * CUDA-event-timed launches (after two warm-up launches) of a kernel that
- * issues only independent DFMA chains from as many CTAs as stay resident
- * (SM count from the device properties).  No counterpart in the paper: it
+ * issues only independent DFMA chains, all three operands in per-thread
+ * registers as in the solve's products, from as many CTAs as stay
+ * resident (SM count from the device properties).  No counterpart in the
+ * paper: it
  * gives the roofline of the FP64 kernels, which on GB300 the FP64 pipe
  * bounds before HBM.  *tflops: 2 * FMAs / second / 1e12.  *sms: the
  * device's SM count.  sink_dev: device double[1], written only if the

@@ -737,11 +737,19 @@ __device__ __forceinline__ double bsell_row_dot_f64(const int* __restrict__ off,
   const int* __restrict__ c = col + (size_t)k0 * R + slot;
   const double* __restrict__ v = val + ((size_t)k0 * R + slot) * (B * B) + r * B;
   double acc = 0.0;
+  // the next batch's columns load one batch ahead, so a batch's x gathers
+  // wait on one memory round trip instead of two (column, then x)
+  int jn[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) jn[u] = ld_nc_s32(c + (size_t)min(u, w - 1) * R);
   for (int k = 0; k < w; k += U) {
     int j[U];
     double a[U][B], xv[U][B];
 #pragma unroll
-    for (int u = 0; u < U; ++u) j[u] = ld_nc_s32(c + (size_t)min(k + u, w - 1) * R);
+    for (int u = 0; u < U; ++u) {
+      j[u] = jn[u];
+      jn[u] = ld_nc_s32(c + (size_t)min(k + U + u, w - 1) * R);
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) ld_run_f64<B, true>(v + (size_t)min(k + u, w - 1) * (R * B * B), a[u]);
 #pragma unroll
