@@ -340,6 +340,40 @@ def test_mixed_vcycle_matches_oracle_on_cast_hierarchy(precision, fmt, monkeypat
             assert rel_inf(z, z64) > 10 * rel_inf(z, ref)
 
 
+@pytest.mark.parametrize("fmt", ["0", "2", "3"])
+@pytest.mark.parametrize("case", ["c1_scalar", "c3_velocity"])
+@pytest.mark.parametrize("precision", [gb.GBS_FP32, gb.GBS_BF16])
+def test_mixed_identity_block_vcycle_matches_oracle(precision, case, fmt, monkeypatch):
+    """A monolithic AMG whose levels are all S (x) I_B in a mixed form: the
+    scalar C1 system (B = 1) and the C3 velocity block run as a system of
+    its own (B = 3).  The finest level's first kernel takes the FP64 input
+    and rounds it (the precision boundary folded into k_iso_cast_mapply),
+    and its last sweep writes the FP64 output; forward and transposed, 1e-5
+    against the oracle's V-cycle on the cast hierarchy, in slices or CSR."""
+    monkeypatch.setenv("GBS_LEVEL_FORMAT", fmt)
+    monkeypatch.setenv("GBS_ISO", "1")
+    if case == "c1_scalar":
+        s = si.make_system("c1", N=10)
+        A = bsr.from_arrays(s.indptr, s.indices, s.data, 1)
+        B = 1
+    else:
+        s = si.make_system("c3", N=10)
+        A = schur.split(bsr.from_arrays(s.indptr, s.indices, s.data, 4), 3).A
+        B = 3
+    Ho = amg.build_hierarchy(A, amg.AmgParams(coarse_enough=60))
+    assert len(Ho.levels) >= 2
+    H = _import(Ho, B, precision=precision)
+    for l in range(len(Ho.levels)):
+        assert gb.level_iso(H, 0, l), l
+    Hc = amg.cast_values(Ho, FMT[precision])
+    rng = np.random.default_rng(47)
+    for tr in (False, True):
+        r = rng.standard_normal(A.shape[0])
+        z = host(gb.apply_precond(H, dev(r), transpose=tr))
+        ref = amg.vcycle(Hc, round_to(r, "fp32"), 0, transpose=tr)
+        assert rel_inf(z, ref) <= 1e-5, (tr, rel_inf(z, ref))
+
+
 @pytest.mark.parametrize("iso", ["1", "0"])
 @pytest.mark.parametrize("fmt", ["0", "0f", "2", "3"])
 @pytest.mark.parametrize("precision", [gb.GBS_FP32, gb.GBS_BF16])
