@@ -249,3 +249,15 @@ def test_velocity_hierarchy_is_identity_blocks(smooth_P):
                 off[:, a, a] = 0.0
             assert not off.any(), l
             assert np.array_equal(v[:, 1, 1], v[:, 0, 0]) and np.array_equal(v[:, 2, 2], v[:, 0, 0]), l
+
+
+def test_iso_blocks_parameter_validated():
+    """iso_blocks takes 0 (level_format decides every level's layout) or 1
+    (levels of identity-multiple blocks stored as S (x) I_B); anything else
+    is rejected before any work."""
+    s = si.make_system("c3", N=4)
+    for v in (0, 1):
+        _host(s, precond=gb.GBS_PC_SCHUR, krylov=gb.GBS_GMRES, coarse_enough=40, iso_blocks=v)
+    with pytest.raises(gb.GbsError) as e:
+        _host(s, precond=gb.GBS_PC_SCHUR, krylov=gb.GBS_GMRES, coarse_enough=40, iso_blocks=2)
+    assert e.value.status == -1
