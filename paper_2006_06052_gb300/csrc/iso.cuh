@@ -10,12 +10,20 @@
 // of the nonzeros stores B of each and the block form B*B values.  The
 // smoother is diag(m) (x) I_B, one value per node.
 //
+// This is a storage form of the statically sized 3x3 velocity blocks of
+// the paper's Section 4 (Listing V3) without their zeros and repeats; the
+// primitives are those of Section 2.3 (residual, relaxation, restriction,
+// prolongation).  A scalar level (B = 1) is S (x) I_1 and takes the same
+// kernels with NV = 1.
+//
 // One lane owns one node (row of S) and applies the row to the node's B
 // interleaved components at once: each value is loaded once for B FMAs,
 // the B gathered x entries of a column are adjacent, and the node's B
 // outputs are formed and stored by the same lane.  The arithmetic per
 // output is the block form's with the zero terms left out, so results
-// agree with it to rounding order.
+// agree with it to rounding order.  Rows of S run one lane each in 32-node
+// slices, or with S lanes (up to a warp) or a 256-thread CTA per row in
+// plain CSR, sized to the level (set_iso_lanes).
 #pragma once
 
 #include "kernels.cuh"
